@@ -1,0 +1,347 @@
+"""Pins of the FP64 oracle against results fixed independently of it.
+
+Each test checks one oracle function against something the paper or the
+mathematics fixes: brute-force formulas on tiny inputs, a dense or FFT solve of
+the same linear system, closed-form motion, conservation laws, the plasma
+frequency and the two-stream dispersion relation.  A dropped term, a wrong
+sign or a swapped weight anywhere in the oracle fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+L4PI = 4.0 * math.pi
+
+
+# --- brute force on tiny inputs -------------------------------------------
+
+def _hat_weights(x, ng, lx):
+    """w[p, g] = max(0, 1 - |x_p - x_g|/dx) over periodic images, with nodes
+    at cell centres (g + 1/2) dx: the linear ("cloud in cell") shape."""
+    dx = lx / ng
+    xg = (np.arange(ng) + 0.5) * dx
+    w = np.zeros((x.size, ng))
+    for shift in (-lx, 0.0, lx):
+        d = np.abs(x[:, None] - xg[None, :] + shift) / dx
+        w += np.maximum(0.0, 1.0 - d)
+    return w
+
+
+@pytest.mark.parametrize("ng,npart", [(1, 3), (2, 5), (3, 8), (5, 7), (8, 8)])
+def test_deposit_matches_hat_function(ng, npart):
+    rng = np.random.default_rng(ng * 31 + npart)
+    lx = 2.5
+    x = rng.uniform(0, lx, npart)
+    x[0] = 0.0                      # left edge
+    p = O.params(ng, npart, lx)
+    q0 = -1.0 * lx / npart          # Q0 = rho_init0 Lx / NP * sign(qoms0)
+    want = 1.0 + (q0 / (lx / ng)) * _hat_weights(x, ng, lx).sum(axis=0)
+    np.testing.assert_allclose(O.deposit(p, x), want, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("ng", [2, 3, 5, 8])
+def test_gather_matches_hat_function(ng):
+    rng = np.random.default_rng(ng)
+    lx, npart = 3.0, 8
+    x = rng.uniform(0, lx, npart)
+    E = rng.standard_normal(ng)
+    p = O.params(ng, npart, lx)
+    want = _hat_weights(x, ng, lx) @ E
+    np.testing.assert_allclose(O.gather(p, x, E), want, rtol=0, atol=1e-13)
+
+
+def test_deposit_at_box_end_is_node_zero_share():
+    # x = Lx is the periodic image of x = 0.
+    p = O.params(4, 1, 4.0)
+    np.testing.assert_allclose(O.deposit(p, [4.0]), O.deposit(p, [0.0]),
+                               atol=1e-15)
+
+
+# --- the field solve against other solvers of the same system ----------------
+
+def _dense_solution(rho, lx):
+    """Eq. 6 for g = 1..NG-1 with Phi_0 = 0, periodic Phi_NG = Phi_0,
+    solved by dense Gaussian elimination (numpy.linalg.solve)."""
+    ng = rho.size
+    dx = lx / ng
+    A = np.zeros((ng, ng))
+    b = np.zeros(ng)
+    A[0, 0] = 1.0
+    for g in range(1, ng):
+        A[g, g] = -2.0
+        A[g, g - 1] = 1.0
+        A[g, (g + 1) % ng] += 1.0
+        b[g] = -rho[g] * dx * dx
+    return np.linalg.solve(A, b)
+
+
+def _neutral_rho(ng, seed):
+    rng = np.random.default_rng(seed)
+    rho = rng.standard_normal(ng)
+    return rho - rho.mean()
+
+
+@pytest.mark.parametrize("ng", [2, 3, 4, 7, 16, 64])
+def test_field_solve_matches_dense_elimination(ng):
+    rho = _neutral_rho(ng, ng)
+    p = O.params(ng, 10, 2.0)
+    np.testing.assert_allclose(O.field_solve(p, rho), _dense_solution(rho, 2.0),
+                               rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("ng", [16, 64, 256, 1024])
+def test_field_solve_matches_fft(ng):
+    # Periodic 3-point Laplacian by FFT: phi_k = rho_k dx^2 / (2 - 2 cos(2 pi k/NG)).
+    rho = _neutral_rho(ng, 7 + ng)
+    lx = L4PI
+    dx = lx / ng
+    k = np.arange(ng)
+    lam = 2.0 - 2.0 * np.cos(2 * np.pi * k / ng)
+    rk = np.fft.fft(rho)
+    ph = np.zeros(ng, complex)
+    ph[1:] = rk[1:] * dx * dx / lam[1:]
+    phi = np.real(np.fft.ifft(ph))
+    phi -= phi[0]
+    got = O.field_solve(O.params(ng, 10, lx), rho)
+    scale = np.abs(phi).max()
+    assert np.abs(got - phi).max() <= 1e-11 * scale
+
+
+def test_efield_of_sine_potential():
+    # Central difference of phi = sin(k x): E = -cos(k x) sin(k dx)/dx exactly.
+    ng, lx = 32, 5.0
+    dx = lx / ng
+    xg = (np.arange(ng) + 0.5) * dx
+    for m in (1, 3, 7):
+        k = 2 * np.pi * m / lx
+        E = O.efield(O.params(ng, 1, lx), np.sin(k * xg))
+        np.testing.assert_allclose(E, -np.cos(k * xg) * np.sin(k * dx) / dx,
+                                   atol=1e-13)
+
+
+def test_converged_cg_equals_direct_solve():
+    # The listing's CG run to convergence reaches the exact solution.
+    x, _ = W.two_stream(20000, L4PI, 0.2, 0.01, 1)
+    p = O.params(64, 20000, L4PI)
+    rho = O.deposit(p, x)
+    phi = O.field_solve(p, rho)
+    phic, it = O.field_cg(p, rho, 150)
+    assert np.abs(phic - phi).max() <= 1e-13 * np.abs(phi).max()
+
+
+def test_cg_150_iterations_unconverged_on_large_grid():
+    # With 64 cells per core, the weak-scaling runs (Sec. 5.2) reach NG >= 256,
+    # where 150 CG iterations do not converge: the direct solve differs.
+    x, _ = W.two_stream(20000, L4PI, 0.2, 0.01, 1)
+    p = O.params(1024, 20000, L4PI)
+    rho = O.deposit(p, x)
+    E = O.efield(p, O.field_solve(p, rho))
+    Ec = O.efield(p, O.field_cg(p, rho, 150)[0])
+    assert np.abs(Ec - E).max() > 0.1 * np.abs(E).max()
+
+
+# --- diagnostics -------------------------------------------------------------
+
+def test_mode_amplitudes_and_field_energy_closed_form():
+    ng, lx = 64, L4PI
+    dx = lx / ng
+    xg = (np.arange(ng) + 0.5) * dx
+    E = 0.3 * np.cos(2 * np.pi * 3 * xg / lx + 0.4)
+    p = O.params(ng, 1, lx)
+    amp = O.mode_amplitudes(p, E, 8)
+    want = np.zeros(8)
+    want[2] = 0.3
+    np.testing.assert_allclose(amp, want, atol=1e-13)
+    # (1/2) sum E^2 dx = (1/2) (A^2/2) Lx for a whole number of periods
+    assert abs(O.field_energy(p, E) - 0.5 * 0.045 * lx) < 1e-13
+
+
+# --- conservation ------------------------------------------------------------
+
+def test_neutrality():
+    x, _ = W.two_stream(20000, L4PI, 0.2, 0.01, 3)
+    p = O.params(64, 20000, L4PI)
+    assert abs(O.deposit(p, x).sum()) < 1e-11
+
+
+def test_total_force_on_particles_vanishes():
+    # CIC deposit + Eq. 6 + Eq. 7 + the same CIC gather: sum_p E(x_p) = 0 for
+    # any particle positions, so the total momentum is conserved.
+    rng = np.random.default_rng(5)
+    for ng, npart in ((8, 3), (64, 1000), (256, 5000)):
+        x = rng.uniform(0, L4PI, npart)
+        p = O.params(ng, npart, L4PI)
+        rho = O.deposit(p, x)
+        _, E = O.field(p, rho)
+        Ex = O.gather(p, x, E)
+        assert abs(Ex.sum()) <= 1e-12 * max(1.0, np.abs(Ex).sum())
+
+
+def test_c1_energy_and_momentum():
+    # The Sec. 4 two-stream run, 200 steps: total energy drifts < 1%, momentum
+    # is conserved to rounding.
+    n = 20000
+    x, v = W.two_stream(n, L4PI, 0.2, 0.01, 11)
+    s = O.State(O.params(64, n, L4PI), x, v)
+    h = s.run(200)
+    m = s.mass
+    ke = 0.5 * m * h[:, 0]
+    tot = ke + h[:, 2]
+    assert (tot.max() - tot.min()) / tot[0] < 0.01
+    mom = m * h[:, 1]
+    assert np.abs(mom - mom[0]).max() <= 1e-12 * m * np.abs(v).sum()
+    # the instability has grown: field energy at the end far above the start
+    assert h[-1, 2] > 100 * h[0, 2]
+
+
+# --- closed-form motion --------------------------------------------------------
+
+def test_single_particle_moves_freely():
+    lx, dt = L4PI, 0.1
+    x0, v0 = 1.234, 0.37
+    s = O.State(O.params(64, 1, lx, dt), [x0], [v0])
+    for n in range(1, 301):
+        s.step()
+        want = math.fmod(x0 + n * v0 * dt, lx)
+        d = abs(s.x[0] - want)
+        assert min(d, lx - d) < 1e-12
+        assert abs(s.v[0] - v0) < 1e-12
+
+
+@pytest.mark.parametrize("d0", [1.0, -1.7, 0.3])
+def test_two_particles_closed_form(d0):
+    # Two electrons in the neutralising ion background: their separation s
+    # obeys s'' = -(s - L/2).  Leapfrog turns this into
+    # d^{n+1} - 2 d^n + d^{n-1} = -dt^2 d^n (d = s - L/2), solved by
+    # d^n = A cos(w n dt) + B sin(w n dt) with sin(w dt/2) = dt/2.  Starting
+    # at rest, d^1 = (1 - dt^2) d^0.
+    lx, dt = L4PI, 0.1
+    s = O.State(O.params(64, 2, lx, dt), [2.0, 2.0 + lx / 2 + d0], [0.0, 0.0])
+    w = 2.0 / dt * math.asin(dt / 2.0)
+    A = d0
+    B = ((1 - dt * dt) * d0 - A * math.cos(w * dt)) / math.sin(w * dt)
+    def d(n):
+        return A * math.cos(w * n * dt) + B * math.sin(w * n * dt)
+
+    for n in range(0, 200):
+        sep = (s.x[1] - s.x[0]) % lx
+        assert abs((sep - lx / 2) - d(n)) < 1e-12, n
+        svv, sv = s.step()
+        # equal and opposite velocities v2 = -v1 = d'/2 with the leapfrog
+        # difference d'^{n+1/2} = (d^{n+1} - d^n)/dt (at rest before step 0),
+        # so the time-centred sum_p v^{n-1/2} v^{n+1/2} = d'^{n-1/2} d'^{n+1/2}/2
+        dm = 0.0 if n == 0 else (d(n) - d(n - 1)) / dt
+        dp = (d(n + 1) - d(n)) / dt
+        assert abs(svv - 0.5 * dm * dp) < 1e-10, n
+        assert abs(sv) < 1e-12
+
+
+# --- plasma oscillation and the two-stream instability -------------------------
+
+def test_langmuir_frequency():
+    # Cold plasma, density perturbation 1e-3 of mode 1: the field energy peaks
+    # twice per plasma period, so peaks are pi/omega apart with omega ~ 1.
+    n, lx, dt = 20000, L4PI, 0.1
+    x, v = W.cold_langmuir(n, lx, 1e-3, 1)
+    s = O.State(O.params(64, n, lx, dt), x, v)
+    fe = s.run(400)[:, 2]
+    peaks = []
+    for i in range(1, fe.size - 1):
+        if fe[i] > fe[i - 1] and fe[i] >= fe[i + 1]:
+            a, b, c = fe[i - 1], fe[i], fe[i + 1]
+            off = 0.5 * (a - c) / (a - 2 * b + c)
+            peaks.append((i + off) * dt)
+    period = (peaks[-1] - peaks[0]) / (len(peaks) - 1)
+    omega = math.pi / period
+    assert len(peaks) >= 10
+    assert abs(omega - 1.0) < 0.01
+
+
+def _fit_rate(hist, dt, t0, t1, mode=1):
+    t = np.arange(hist.shape[0]) * dt
+    sel = (t >= t0) & (t <= t1)
+    amp = hist[sel, 2 + mode]
+    return np.polyfit(t[sel], np.log(amp), 1)[0]
+
+
+def _golden_rates():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "two_stream_rates.txt"))
+            if l.strip() and not l.startswith("#")]
+    return {round(float(a), 6): float(g) for a, g in rows}
+
+
+L_FAST = 2 * math.pi * 0.2 / math.sqrt(0.375)   # mode 1 at a^2 = 3/8
+
+
+@pytest.mark.parametrize("lx,vth,t0,t1", [(L4PI, 0.0, 2.0, 12.0),
+                                          (L_FAST, 0.0, 2.0, 12.0),
+                                          (L_FAST, 0.01, 2.0, 12.0)])
+def test_two_stream_growth_rate(lx, vth, t0, t1):
+    # Growing-eigenmode seed of mode 1; ln|E_1| grows at the rate of the cold
+    # two-stream dispersion relation (tests/golden/two_stream_rates.txt).
+    # In the Sec. 4 box (a = k v0 = 0.1 ~ gamma) the beams' charge
+    # perturbations nearly cancel at t = 0, so the thermal noise of vth = 0.01
+    # swamps mode 1 there; that box is checked cold.
+    n, v0, dt = 20000, 0.2, 0.1
+    k = 2 * math.pi / lx
+    gamma = _golden_rates()[round(k * v0, 6)]
+    assert abs(gamma - W.cold_two_stream_gamma(k, v0)) < 1e-5
+    x, v = W.two_stream_eigenmode(n, lx, v0, vth, 1e-3, 1, 5)
+    s = O.State(O.params(64, n, lx, dt), x, v)
+    h = s.run(int(t1 / dt) + 2)
+    rate = _fit_rate(h, dt, t0, t1)
+    assert abs(rate - gamma) / gamma < 0.05, (rate, gamma)
+
+
+# --- the paper's cycle order ----------------------------------------------------
+
+def test_paper_order_equals_library_order():
+    # nt Appendix A cycles (drift, deposit, solve, E, kick) = one
+    # drift+deposit+solve, nt-1 library steps, and a final gather + kick.
+    n, lx, nt = 5000, L4PI, 25
+    x, v = W.two_stream(n, lx, 0.2, 0.01, 2)
+    p = O.params(32, n, lx)
+    a = O.State(p, x, v)
+    a.run_paper_order(nt)
+
+    xb = O.drift(p, v, x)
+    b = O.State(p, xb, v)
+    for _ in range(nt - 1):
+        b.step()
+    vb = O.kick(p, O.gather(p, b.x, b.E), b.v)
+    assert np.array_equal(a.x, b.x)
+    assert np.array_equal(a.v, vb)
+    assert np.array_equal(a.E, b.E)
+
+
+# --- the fixed-point deposit (reading R5) ---------------------------------------
+
+def test_fixed_deposit_golden_cases():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "fixed_deposit_dyadic.txt"))
+            if l.strip() and not l.startswith("#")]
+    for r in rows:
+        x = np.array([float(r[0])], dtype=np.float32)
+        want = np.array([int(t) for t in r[1:]], dtype=np.int64)
+        np.testing.assert_array_equal(O.deposit_fixed(4, 4.0, x), want)
+
+
+def test_fixed_deposit_exact_total_and_fp64_agreement():
+    n, ng, lx = 20000, 64, L4PI
+    x, v = W.two_stream(n, lx, 0.2, 0.01, 4)
+    x32, _ = W.to_f32_state(x, v, lx)
+    rq = O.deposit_fixed(ng, lx, x32)
+    assert int(rq.sum()) == n * (1 << O.FIX_BITS)
+    assert rq.min() >= 0
+    p = O.params(ng, n, lx)
+    rho_fix = O.rho_from_fixed(p, rq)
+    rho64 = O.deposit(p, x32.astype(np.float64))
+    # per particle the float32 fraction differs from the FP64 weight by at
+    # most a few units of 2^-24 * NG, so rho differs by <~ (NG/N) * count * that
+    assert np.abs(rho_fix - rho64).max() < 1e-5
+    assert abs(rho_fix.sum()) < 1e-10
