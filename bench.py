@@ -1,0 +1,352 @@
+#!/usr/bin/env python3
+"""Benchmark of the 1D electrostatic PIC step on GB300.
+
+Workload (default): the single large run -- 2^26 electrons, 4096 cells,
+L = 4 pi, two beams at +-0.2 with thermal spread 0.01, modes 1..8 perturbed at
+1e-4 with seeded random phases, dt = 0.1, counting sort every 20 steps; float32
+push, int64 fixed-point deposit, float64 field solve.  A "step" is one whole
+PIC step: [sort if due] + fused gather/push/deposit + field solve.
+
+Prints one JSON line (rank 0).  `value` is particle-steps/s with the state
+resident in HBM; `e2e` is the same metric through the public API from pinned
+host buffers (upload the initial state, run the steps, read back the
+diagnostics and the final state); `roofline` is the fused push kernel's
+algorithmic bytes (16 B per particle: x, v read and written, float32) over its
+CUDA-event duration against the measured copy bandwidth; `cpu_baseline` is the
+FP64 oracle on this host.
+
+`--impl reference` times the FP64 oracle (the reference arm) on the same
+workload: each step is the oracle's step over a bounded sample of 2^20
+particles of the same state.
+Under torchrun each rank runs its own independent run (weak scaling, no
+collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_PARTICLE_STEP = 16          # x, v float32 read + write
+C2 = dict(npart=1 << 26, ncell=4096, length=4.0 * math.pi, dt=0.1, v0=0.2,
+          vth=0.01, eps=1e-4, sort_interval=20, seed=2026)
+SMALL = dict(npart=1 << 20, ncell=4096, length=4.0 * math.pi, dt=0.1, v0=0.2,
+             vth=0.01, eps=1e-4, sort_interval=20, seed=2026)
+REF_SAMPLE = 1 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "small"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--variant", type=int, default=0)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--bps", type=int, default=0)
+    return ap.parse_args()
+
+
+def workload(name):
+    return dict(C2) if name == "c2" else dict(SMALL)
+
+
+def make_state(w):
+    import workloads as W
+    x, v = W.two_stream(w["npart"], w["length"], w["v0"], w["vth"], w["seed"],
+                        modes=W.two_stream_modes_1_to_8(w["eps"], w["seed"]))
+    return W.to_f32_state(x, v, w["length"])
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax = max(smax, float(f[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the fused push from the committed ncu summary,
+    if the kernel source is unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", "push_fixed_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    src = os.path.join(ROOT, "paper_1108_1954_gb300", "csrc", "push.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if rec.get("push_cu_sha256") != sha:
+        return None
+    return rec.get("bytes_per_launch_c2")
+
+
+def time_ours(args, w, x32, v32):
+    import numpy as np
+    import torch
+    import paper_1108_1954_gb300 as pic
+
+    n, S = w["npart"], w["sort_interval"]
+    params = pic.Params(npart=n, ncell=w["ncell"], length=w["length"], dt=w["dt"],
+                        sort_interval=S, history=8192, deposit_variant=args.variant,
+                        block_size=args.block, blocks_per_sm=args.bps)
+    run = pic.Run(params, device="cuda")
+    stream = run.stream
+    run.init(x32, v32)
+    launches = {"n": 0}
+
+    def one_step(ev=None):
+        if S > 0 and run.step > 0 and run.step % S == 0:
+            run.sort()
+            launches["n"] += 4
+        if ev is not None:
+            ev[0].record(stream)
+        run.push()
+        if ev is not None:
+            ev[1].record(stream)
+        run.solve_field()
+        launches["n"] += 2
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    K = args.steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(K)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(torch.cuda.current_device())
+    ws, rank, _ = dist_env()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches["n"] = 0
+    clocks.start()
+    t0.record(stream)
+    for i in range(K):
+        one_step(evs[i])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    total_ms = t0.elapsed_time(t1)
+    push_ms = [a.elapsed_time(b) for a, b in evs]
+    run.sync()
+    grid, block, variant = run.launch_shape()
+    diag = run.diagnostics(run.step - 1, 1)[0]
+    res = dict(total_ms=total_ms, push_ms=push_ms, clocks=ck, launches=launches["n"],
+               grid=grid, block=block, variant=variant, steps=K,
+               energy=float(diag["kinetic"] + diag["field"]))
+    run.close()
+    return res
+
+
+def time_e2e(args, w, x32, v32):
+    """The public API end to end: pinned host state -> pic_init -> pic_step_n
+    -> diagnostics + final state back to pinned host memory."""
+    import torch
+    import paper_1108_1954_gb300 as pic
+    n, K = w["npart"], args.steps
+    xh = torch.from_numpy(x32).pin_memory()
+    vh = torch.from_numpy(v32).pin_memory()
+    xo = torch.empty_like(xh).pin_memory()
+    vo = torch.empty_like(vh).pin_memory()
+    params = pic.Params(npart=n, ncell=w["ncell"], length=w["length"], dt=w["dt"],
+                        sort_interval=w["sort_interval"], history=max(8192, K + 1),
+                        deposit_variant=args.variant, block_size=args.block,
+                        blocks_per_sm=args.bps)
+    run = pic.Run(params, device="cuda")
+    run.init(xh, vh)                      # warm: graph capture, first touch
+    run.step_n(w["sort_interval"] + 1)
+    run.sync()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    run.init(xh, vh)
+    run.step_n(K)
+    d = run.diagnostics(0, K)
+    run.get_state(xo, vo)
+    el = time.perf_counter() - t
+    run.close()
+    h2d = 2 * 4 * n
+    d2h = 2 * 4 * n + d.nbytes
+    return dict(value=n * K / el, seconds=el, h2d_per_step=h2d / K, d2h_per_step=d2h / K)
+
+
+def time_oracle(w, x32, v32, budget_s=12.0, sample=None, steps=None):
+    """The FP64 oracle, single thread, on the same state (or its first
+    `sample` particles): particle-steps/s."""
+    import numpy as np
+    import oracle as O
+    n = w["npart"] if sample is None else min(sample, w["npart"])
+    x = x32[:n].astype(np.float64)
+    v = v32[:n].astype(np.float64)
+    st = O.State(O.params(w["ncell"], n, w["length"], w["dt"]), x, v)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        st.step()
+        done += 1
+        el = time.perf_counter() - t0
+        if steps is not None and done >= steps:
+            break
+        if steps is None and el >= budget_s:
+            break
+    return dict(value=n * done / el, steps=done, npart=n, seconds=el)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    w = workload(args.workload)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        x32, v32 = make_state(w)
+        K, Wm = args.steps, args.warmup
+        time_oracle(w, x32, v32, sample=REF_SAMPLE, steps=max(1, Wm))
+        r = time_oracle(w, x32, v32, sample=REF_SAMPLE, steps=max(1, K))
+        line = {
+            "impl": "reference", "metric": "particle-steps/s",
+            "value": r["value"], "unit": "particle-steps/s", "n_gpus": args.gpus,
+            "steps": K, "warmup": Wm, "ms_per_step": 1e3 * r["seconds"] / r["steps"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "single large run, %d electrons, %d cells (oracle sample %d)"
+                       % (w["npart"], w["ncell"], r["npart"])},
+            "cpu_baseline": {"value": r["value"], "unit": "particle-steps/s", "cores": 1,
+                             "kind": "oracle",
+                             "sample": "FP64 oracle, first %d particles of the state, %d steps"
+                             % (r["npart"], r["steps"])},
+            "e2e": {"value": r["value"], "unit": "particle-steps/s",
+                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line))
+        return
+
+    import torch
+    if ws > 1:
+        torch.distributed.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    x32, v32 = make_state(w)
+    res = time_ours(args, w, x32, v32)
+    e2e = None if args.no_e2e else time_e2e(args, w, x32, v32)
+
+    n, K = w["npart"], res["steps"]
+    total_s = res["total_ms"] / 1e3
+    if ws > 1:
+        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = ws * n * K / total_s
+    push_avg_s = statistics.mean(res["push_ms"]) / 1e3
+    achieved = BYTES_PER_PARTICLE_STEP * n / push_avg_s / 1e9
+    peak, src = measured_peak()
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        c = time_oracle(w, x32, v32, budget_s=12.0)
+        cpu = {"value": c["value"], "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+               "sample": "FP64 oracle on the full %d-particle state, first %d steps (%.1f s)"
+               % (c["npart"], c["steps"], c["seconds"])}
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return
+    line = {
+        "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s",
+        "n_gpus": ws, "steps": K, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_s / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "single large run: %d electrons, %d cells, L=4pi, two-stream "
+                               "+-0.2 vth 0.01, modes 1-8 at 1e-4, dt 0.1, sort every %d steps"
+                               % (n, w["ncell"], w["sort_interval"]),
+                   "npart": n, "ncell": w["ncell"], "sort_interval": w["sort_interval"],
+                   "precision": "f32 push, int64 fixed-point deposit, f64 field solve",
+                   "l2": "inputs larger than L2 (%.0f MiB particle state)" % (16 * n / 2**20 / 2),
+                   "launch": {"grid": res["grid"], "block": res["block"],
+                              "deposit_variant": res["variant"]}},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": recorded_traffic(),
+                     "kernel": "pic_push_fixed_kernel", "peak_source": src,
+                     "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP,
+                     "push_ms_avg": push_avg_s * 1e3},
+        "gpu_launches": res["launches"],
+        "clocks": res["clocks"],
+    }
+    if e2e is not None:
+        line["e2e"] = {"value": e2e["value"], "unit": "particle-steps/s",
+                       "h2d_bytes_per_step": e2e["h2d_per_step"],
+                       "d2h_bytes_per_step": e2e["d2h_per_step"]}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

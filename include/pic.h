@@ -1,0 +1,200 @@
+/*
+ * pic.h -- C ABI of the GB300 (sm_103a) library for the 1D electrostatic
+ * electron Particle-in-Cell step of Markidis & Lapenta, "Development and
+ * performance analysis of a UPC Particle-in-Cell code" (PGAS10).
+ *
+ * The method (Sec. 2): N electrons on a periodic line of length L cut into
+ * NG cells of width dx = L/NG, nodes at the cell centres (g + 1/2) dx,
+ * immobile neutralising ions of density rho_ion, charge-to-mass ratio qm < 0,
+ * time step dt.  One step advances the state (x^n, v^{n-1/2}, E^n):
+ *   gather   E_p = linear interpolation of E^n at x^n       (Sec. 2.3)
+ *   kick     v^{n+1/2} = v^{n-1/2} + qm E_p dt              (Sec. 2.1, Eq. 3)
+ *   drift    x^{n+1} = x^n + v^{n+1/2} dt, wrapped to [0,L) (Sec. 2.1, Eq. 2)
+ *   deposit  linear weighting of x^{n+1} onto the nodes     (Sec. 2.3)
+ *   solve    Phi_{g+1} - 2 Phi_g + Phi_{g-1} = -rho_g dx^2  (Sec. 2.2, Eq. 6)
+ *   field    E_g = -(Phi_{g+1} - Phi_{g-1}) / (2 dx)        (Sec. 2.2, Eq. 7)
+ *
+ * Precision (PIC_FP32_FIXED, the default): positions and velocities are
+ * float32; the deposit is exact integer arithmetic on 2^-24 fractions of a
+ * particle (below), so the density is the same integer for any launch shape
+ * or particle order; the field solve and all diagnostics are float64.
+ *
+ * Fixed-point deposit (the library's exact form of the Sec. 2.3 weighting).
+ * With c = (float)(NG / L) and float operations rounded to nearest:
+ *   u = x*c, s = u - 0.5f, i = floorf(s), f = s - i, W = trunc(f * 2^24);
+ *   rho_q[(i+1) mod NG] += W,  rho_q[i mod NG] += 2^24 - W.
+ * The float64 density is rho_g = rho_ion - rho_ion (NG/N) rho_q[g] 2^-24.
+ *
+ * Ownership.  The caller owns all device memory: it allocates one workspace
+ * of pic_workspace_size() bytes (any allocator; 256-byte alignment) and the
+ * library carves every device array out of it.  The library allocates no
+ * device memory.  It keeps a small host-side handle (pic_run) and CUDA graphs.
+ * All work is enqueued on the caller's stream; calls return before the GPU
+ * finishes, except those documented as synchronising.
+ *
+ * Errors.  Every int-returning call returns PIC_OK (0) or a negative code.
+ * Kernels never trap: a particle with a non-finite or out-of-range position
+ * sets a device error word, which the synchronising calls (pic_sync,
+ * pic_diagnostics, pic_get_state, pic_get_field) report as PIC_EDEVICE.
+ *
+ * Threading.  Calls on one run are not thread-safe; different runs are.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_ABI_VERSION 1
+
+/* Return codes. */
+#define PIC_OK 0
+#define PIC_EINVAL (-1)   /* bad argument or parameter                       */
+#define PIC_ENOMEM (-2)   /* workspace too small / pool budget exhausted      */
+#define PIC_ECUDA (-3)    /* a CUDA runtime call failed                       */
+#define PIC_ETIMEOUT (-4) /* a bounded device wait ran out                     */
+#define PIC_EDEVICE (-5)  /* a kernel flagged bad particle data                */
+#define PIC_ESTATE (-6)   /* call out of order (e.g. push before init)         */
+
+/* Precision modes. */
+#define PIC_FP32_FIXED 0  /* float32 push, int64 fixed-point deposit (default) */
+#define PIC_FP32_ATOMIC 1 /* float32 push, float32 atomic deposit              */
+#define PIC_FP64 2        /* float64 push, float64 atomic deposit              */
+
+/* Deposit-kernel variants of the fused push (PIC_FP32_FIXED only). */
+#define PIC_DEPOSIT_AUTO 0   /* chosen by the library                        */
+#define PIC_DEPOSIT_ATOMIC 1 /* two shared-memory atomics per particle       */
+#define PIC_DEPOSIT_MATCH 2  /* warp groups of equal cell (match + reduce)   */
+#define PIC_DEPOSIT_PACKED 3 /* count and weight packed in one atomic        */
+#define PIC_DEPOSIT_MATCH_PACKED 4 /* warp groups, one packed atomic each   */
+
+#define PIC_NCELL_MAX 8192  /* largest NG (the per-block density tile)       */
+#define PIC_NMODES 8        /* Fourier modes recorded per step               */
+
+/* Parameters of one run (Sec. 2; names follow the paper's symbols). */
+typedef struct pic_params {
+    int64_t npart;         /* N, particles (>= 1)                             */
+    int32_t ncell;         /* NG, cells (1 .. PIC_NCELL_MAX)                   */
+    int32_t precision;     /* PIC_FP32_FIXED | PIC_FP32_ATOMIC | PIC_FP64      */
+    double length;         /* L > 0                                           */
+    double dt;             /* time step > 0                                   */
+    double qm;             /* charge-to-mass ratio, < 0 (electrons: -1)        */
+    double rho_ion;        /* ion background density > 0 (paper: 1)            */
+    int32_t sort_interval; /* counting sort by cell every S steps (0 = never)  */
+    int32_t history;       /* rows of the device diagnostics ring (>= 1)       */
+    int32_t deposit_variant; /* PIC_DEPOSIT_*                                 */
+    int32_t block_size;    /* threads per block of the fused push (0 = auto)   */
+    int32_t blocks_per_sm; /* resident blocks per SM of the fused push (0=auto)*/
+    int32_t reserved;      /* must be 0                                       */
+} pic_params;
+
+/* One row of the per-step diagnostics (all float64 on the device). */
+typedef struct pic_diag_row {
+    int64_t step;          /* n                                               */
+    double kinetic;        /* KE^n = (1/2) m sum_p v^{n-1/2} v^{n+1/2};  NaN
+                              until the push of step n has run                 */
+    double momentum;       /* m sum_p v^{n+1/2} (NaN likewise)                 */
+    double field;          /* (1/2) dx sum_g (E^n_g)^2                          */
+    double charge;         /* dx sum_g rho^n_g (0 for a neutral box)           */
+    int64_t charge_q;      /* sum_g rho_q^n (= N 2^24 exactly in FIXED mode)    */
+    double mode[PIC_NMODES]; /* 2 |(1/NG) sum_g E^n_g e^{-2 pi i m g/NG}|,
+                                m = 1..8                                       */
+} pic_diag_row;
+
+typedef struct pic_run pic_run;
+
+/* Library ABI version (PIC_ABI_VERSION). */
+int pic_version(void);
+
+/* Static text for a return code. */
+const char *pic_strerror(int code);
+
+/* Bytes of device workspace a run with parameters *p needs.
+ * Returns PIC_EINVAL for invalid parameters. */
+int pic_workspace_size(const pic_params *p, size_t *bytes);
+
+/* Create a run on the current CUDA device.  workspace: caller-owned device
+ * memory of at least pic_workspace_size() bytes, 256-byte aligned, kept alive
+ * until pic_destroy.  stream: a cudaStream_t (NULL = legacy default stream).
+ * Validates parameters (PIC_EINVAL), reads the device's SM count and picks the
+ * launch shape.  Enqueues nothing. */
+int pic_create(const pic_params *p, void *workspace, size_t workspace_bytes,
+               void *stream, pic_run **out);
+
+/* Release the host handle and its CUDA graphs (not the workspace). */
+void pic_destroy(pic_run *run);
+
+/* Load the initial state and make E^0 ready (Sec. 2 "initialization"; the
+ * Appendix A set-up).  x0, v0: host arrays of N values in the run's precision
+ * (float for the FP32 modes, double for PIC_FP64); v0 is v^{-1/2}.  Positions
+ * must lie in [0, L).  Copies them to the device, deposits rho^0, solves Phi^0
+ * and E^0 and resets the step counter to 0.  Synchronises the stream (the host
+ * arrays may be reused on return).  PIC_EINVAL for positions outside [0, L). */
+int pic_init(pic_run *run, const void *x0, const void *v0);
+
+/* Charge deposit (Sec. 2.3) of the current positions into the density
+ * accumulator, which it zeroes first.  Asynchronous. */
+int pic_deposit(pic_run *run);
+
+/* Field solve (Sec. 2.2, Eqs. 6-7) of the accumulated density: rho, Phi
+ * (Phi_0 = 0), E in float64 and the float32 copy used by the gather; records
+ * field energy and modes for the current step and clears the accumulator.
+ * Asynchronous. */
+int pic_solve_field(pic_run *run);
+
+/* Fused gather, kick, drift, wrap and deposit of x^{n+1} (Sec. 2.1 Eqs. 2-3,
+ * Sec. 2.3) for all particles; rho_q then holds the fixed-point density of
+ * x^{n+1}.  Follow it with pic_solve_field to finish the step.  Asynchronous. */
+int pic_push(pic_run *run);
+
+/* Counting sort of the particles by cell (stable: particles of one cell keep
+ * their order).  Changes no physical quantity.  Asynchronous. */
+int pic_sort(pic_run *run);
+
+/* n whole steps: [sort if due] + push + solve, replayed from CUDA graphs.
+ * A step n with n % S == 0 (S = sort_interval > 0, n > 0) sorts first.
+ * Asynchronous. */
+int pic_step_n(pic_run *run, int64_t n);
+
+/* Wait for the stream, then report the device error word (PIC_EDEVICE). */
+int pic_sync(pic_run *run);
+
+/* Copy the diagnostics rows of steps [first, first + count) (each must still
+ * be in the history ring) to rows[] on the host.  Synchronises. */
+int pic_diagnostics(pic_run *run, int64_t first, int32_t count,
+                    pic_diag_row *rows);
+
+/* Current step number n (host-side count of completed steps). */
+int64_t pic_step_count(const pic_run *run);
+
+/* Copy x^n, v^{n-1/2} (N values each, run precision) to host arrays, in the
+ * current particle order.  Synchronises. */
+int pic_get_state(pic_run *run, void *x, void *v);
+
+/* Replace x, v with host arrays (a checkpoint restore) and set the step
+ * counter to `step`; re-deposits and re-solves like pic_init. Synchronises. */
+int pic_set_state(pic_run *run, const void *x, const void *v, int64_t step);
+
+/* Copy the grid of the last solve to host arrays (any may be NULL):
+ * rho[NG], phi[NG], E[NG] float64 and rho_q[NG] (the fixed-point sums that
+ * solve consumed; FIXED mode only, else zeros).  Synchronises. */
+int pic_get_field(pic_run *run, double *rho, double *phi, double *E,
+                  int64_t *rho_q);
+
+/* Device pointers of the current particle arrays (they alternate after each
+ * sort) and of the float32 field used by the gather. */
+int pic_device_arrays(pic_run *run, void **x, void **v, void **E32);
+
+/* The launch shape the run uses for its fused push. */
+int pic_launch_shape(const pic_run *run, int32_t *grid, int32_t *block,
+                     int32_t *variant);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIC_H */

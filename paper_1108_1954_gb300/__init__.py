@@ -1,0 +1,279 @@
+"""Python binding of libpic, the GB300 (sm_103a) library for the 1D
+electrostatic electron Particle-in-Cell step of Markidis & Lapenta (PGAS10).
+
+This module marshals arguments only: every step of the method runs in the
+CUDA kernels behind the C ABI of `include/pic.h`.  PyTorch supplies the device
+memory (one workspace tensor per run) and the CUDA stream.  There is no CPU
+fallback: importing this package fails if `_build/libpic.so` has not been
+built (`python -c "import __graft_entry__ as g; g.build()"`).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpic.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        "libpic.so is not built (%s); build it with paper_1108_1954_gb300.build"
+        " or __graft_entry__.build() -- there is no CPU fallback" % LIB_PATH)
+
+_lib = C.CDLL(LIB_PATH)
+
+# --- constants of include/pic.h ------------------------------------------------
+PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA = 0, -1, -2, -3
+PIC_ETIMEOUT, PIC_EDEVICE, PIC_ESTATE = -4, -5, -6
+PIC_FP32_FIXED, PIC_FP32_ATOMIC, PIC_FP64 = 0, 1, 2
+PIC_DEPOSIT_AUTO, PIC_DEPOSIT_ATOMIC, PIC_DEPOSIT_MATCH = 0, 1, 2
+PIC_DEPOSIT_PACKED, PIC_DEPOSIT_MATCH_PACKED = 3, 4
+PIC_NCELL_MAX = 8192
+PIC_NMODES = 8
+FIX_BITS = 24
+
+VARIANT_NAMES = {PIC_DEPOSIT_ATOMIC: "atomic", PIC_DEPOSIT_MATCH: "match",
+                 PIC_DEPOSIT_PACKED: "packed",
+                 PIC_DEPOSIT_MATCH_PACKED: "match_packed"}
+
+
+class CParams(C.Structure):
+    _fields_ = [("npart", C.c_int64), ("ncell", C.c_int32),
+                ("precision", C.c_int32), ("length", C.c_double),
+                ("dt", C.c_double), ("qm", C.c_double),
+                ("rho_ion", C.c_double), ("sort_interval", C.c_int32),
+                ("history", C.c_int32), ("deposit_variant", C.c_int32),
+                ("block_size", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class CDiagRow(C.Structure):
+    _fields_ = [("step", C.c_int64), ("kinetic", C.c_double),
+                ("momentum", C.c_double), ("field", C.c_double),
+                ("charge", C.c_double), ("charge_q", C.c_int64),
+                ("mode", C.c_double * PIC_NMODES)]
+
+
+DIAG_DTYPE = np.dtype([("step", np.int64), ("kinetic", np.float64),
+                       ("momentum", np.float64), ("field", np.float64),
+                       ("charge", np.float64), ("charge_q", np.int64),
+                       ("mode", np.float64, (PIC_NMODES,))])
+assert DIAG_DTYPE.itemsize == C.sizeof(CDiagRow)
+
+_P = C.POINTER(CParams)
+_VP = C.c_void_p
+_SIG = {
+    "pic_version": (C.c_int, []),
+    "pic_strerror": (C.c_char_p, [C.c_int]),
+    "pic_workspace_size": (C.c_int, [_P, C.POINTER(C.c_size_t)]),
+    "pic_create": (C.c_int, [_P, _VP, C.c_size_t, _VP, C.POINTER(_VP)]),
+    "pic_destroy": (None, [_VP]),
+    "pic_init": (C.c_int, [_VP, _VP, _VP]),
+    "pic_deposit": (C.c_int, [_VP]),
+    "pic_solve_field": (C.c_int, [_VP]),
+    "pic_push": (C.c_int, [_VP]),
+    "pic_sort": (C.c_int, [_VP]),
+    "pic_step_n": (C.c_int, [_VP, C.c_int64]),
+    "pic_sync": (C.c_int, [_VP]),
+    "pic_diagnostics": (C.c_int, [_VP, C.c_int64, C.c_int32, _VP]),
+    "pic_step_count": (C.c_int64, [_VP]),
+    "pic_get_state": (C.c_int, [_VP, _VP, _VP]),
+    "pic_set_state": (C.c_int, [_VP, _VP, _VP, C.c_int64]),
+    "pic_get_field": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "pic_device_arrays": (C.c_int, [_VP, C.POINTER(_VP), C.POINTER(_VP),
+                                    C.POINTER(_VP)]),
+    "pic_launch_shape": (C.c_int, [_VP, C.POINTER(C.c_int32),
+                                   C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+}
+for _name, (_res, _args) in _SIG.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+assert _lib.pic_version() == 1, "libpic ABI version mismatch"
+
+
+class PicError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (what, strerror(code), code))
+
+
+def strerror(code: int) -> str:
+    return _lib.pic_strerror(int(code)).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != PIC_OK:
+        raise PicError(rc, what)
+
+
+def _ptr(a) -> int:
+    """Address of a C-contiguous numpy array or a torch tensor's storage."""
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+@dataclass
+class Params:
+    """Run parameters (pic_params of include/pic.h)."""
+    npart: int
+    ncell: int
+    length: float
+    dt: float = 0.1
+    qm: float = -1.0
+    rho_ion: float = 1.0
+    precision: int = PIC_FP32_FIXED
+    sort_interval: int = 0
+    history: int = 0
+    deposit_variant: int = PIC_DEPOSIT_AUTO
+    block_size: int = 0
+    blocks_per_sm: int = 0
+
+    def c(self) -> CParams:
+        return CParams(int(self.npart), int(self.ncell), int(self.precision),
+                       float(self.length), float(self.dt), float(self.qm),
+                       float(self.rho_ion), int(self.sort_interval),
+                       int(self.history), int(self.deposit_variant),
+                       int(self.block_size), int(self.blocks_per_sm), 0)
+
+    @property
+    def dtype(self):
+        return np.float64 if self.precision == PIC_FP64 else np.float32
+
+
+def workspace_size(p: Params) -> int:
+    n = C.c_size_t(0)
+    cp = p.c()
+    _check(_lib.pic_workspace_size(C.byref(cp), C.byref(n)), "pic_workspace_size")
+    return int(n.value)
+
+
+class Run:
+    """One PIC run on a CUDA device; its workspace is a torch uint8 tensor."""
+
+    def __init__(self, p: Params, device=None, stream=None):
+        import torch
+        self.p = p
+        self.device = torch.device(device if device is not None else "cuda")
+        nbytes = workspace_size(p)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            handle = _VP()
+            cp = p.c()
+            _check(_lib.pic_create(C.byref(cp), _VP(self.workspace.data_ptr()),
+                                   nbytes, _VP(self.stream.cuda_stream),
+                                   C.byref(handle)), "pic_create")
+        self._h = handle
+
+    # --- lifecycle ----------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.pic_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _host(self, a):
+        if isinstance(a, np.ndarray):
+            return np.ascontiguousarray(a, dtype=self.p.dtype)
+        return a  # a contiguous CPU torch tensor of the run's dtype
+
+    # --- the C ABI, one method per entry point -------------------------------
+    def init(self, x0, v0):
+        x0, v0 = self._host(x0), self._host(v0)
+        _check(_lib.pic_init(self._h, _VP(_ptr(x0)), _VP(_ptr(v0))), "pic_init")
+
+    def set_state(self, x, v, step: int):
+        x, v = self._host(x), self._host(v)
+        _check(_lib.pic_set_state(self._h, _VP(_ptr(x)), _VP(_ptr(v)), int(step)),
+               "pic_set_state")
+
+    def deposit(self):
+        _check(_lib.pic_deposit(self._h), "pic_deposit")
+
+    def solve_field(self):
+        _check(_lib.pic_solve_field(self._h), "pic_solve_field")
+
+    def push(self):
+        _check(_lib.pic_push(self._h), "pic_push")
+
+    def sort(self):
+        _check(_lib.pic_sort(self._h), "pic_sort")
+
+    def step_n(self, n: int):
+        _check(_lib.pic_step_n(self._h, int(n)), "pic_step_n")
+
+    def sync(self):
+        _check(_lib.pic_sync(self._h), "pic_sync")
+
+    @property
+    def step(self) -> int:
+        return int(_lib.pic_step_count(self._h))
+
+    def diagnostics(self, first: int = 0, count: int | None = None) -> np.ndarray:
+        if count is None:
+            count = self.step - first + 1
+        out = np.zeros(count, dtype=DIAG_DTYPE)
+        _check(_lib.pic_diagnostics(self._h, int(first), int(count), _VP(out.ctypes.data)),
+               "pic_diagnostics")
+        return out
+
+    def get_state(self, x=None, v=None):
+        if x is None:
+            x = np.empty(self.p.npart, dtype=self.p.dtype)
+        if v is None:
+            v = np.empty(self.p.npart, dtype=self.p.dtype)
+        _check(_lib.pic_get_state(self._h, _VP(_ptr(x)), _VP(_ptr(v))), "pic_get_state")
+        return x, v
+
+    def get_field(self):
+        ng = self.p.ncell
+        rho, phi, E = np.zeros(ng), np.zeros(ng), np.zeros(ng)
+        rq = np.zeros(ng, dtype=np.int64)
+        _check(_lib.pic_get_field(self._h, _VP(rho.ctypes.data), _VP(phi.ctypes.data),
+                                  _VP(E.ctypes.data), _VP(rq.ctypes.data)), "pic_get_field")
+        return dict(rho=rho, phi=phi, E=E, rho_q=rq)
+
+    def device_arrays(self):
+        """Torch views (x, v, E32) of the current device arrays."""
+        import torch
+        x, v, e = _VP(), _VP(), _VP()
+        _check(_lib.pic_device_arrays(self._h, C.byref(x), C.byref(v), C.byref(e)),
+               "pic_device_arrays")
+        base = self.workspace.data_ptr()
+        tdt = torch.float64 if self.p.precision == PIC_FP64 else torch.float32
+        es = 8 if self.p.precision == PIC_FP64 else 4
+        n = self.p.npart
+
+        def view(addr, count, dt, size):
+            off = addr - base
+            return self.workspace[off:off + count * size].view(dt)
+        return (view(x.value, n, tdt, es), view(v.value, n, tdt, es),
+                view(e.value, self.p.ncell, torch.float32, 4))
+
+    def launch_shape(self):
+        g, b, v = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(_lib.pic_launch_shape(self._h, C.byref(g), C.byref(b), C.byref(v)),
+               "pic_launch_shape")
+        return int(g.value), int(b.value), int(v.value)
+
+
+def header_functions(header_path: str | None = None):
+    """Names of the functions include/pic.h declares."""
+    import re
+    if header_path is None:
+        header_path = os.path.join(os.path.dirname(_HERE), "include", "pic.h")
+    text = open(header_path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pic_[a-z0-9_]+)\s*\(", text)))

@@ -1,0 +1,577 @@
+// pic_api.cu -- the C ABI of include/pic.h: parameter checks, the workspace
+// layout, the run handle, step sequencing and CUDA-graph replay.
+//
+// The caller owns every device byte (one workspace); this file only carves it.
+// A step is [sort if due] + fused push/deposit + field solve, enqueued on the
+// caller's stream.  pic_step_n replays whole sort periods from CUDA graphs
+// (captured once per run on a private stream, launched on the caller's), so a
+// period of S steps costs one graph launch instead of 2 S + 4 kernel launches.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "pic_internal.cuh"
+
+using namespace pic;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kMaxPushGrid = 4096;     // per-block partial sums kept
+constexpr int kMaxSortChunks = 1024;
+constexpr int kPlainBlock = 16;        // steps per graph when not sorting
+constexpr int kDefaultHistory = 4096;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+int validate(const pic_params *p) {
+    if (!p) return PIC_EINVAL;
+    if (p->npart < 1 || p->npart > (int64_t)0xFFFFFFFFll) return PIC_EINVAL;
+    if (p->ncell < 1 || p->ncell > PIC_NCELL_MAX) return PIC_EINVAL;
+    if (p->precision < PIC_FP32_FIXED || p->precision > PIC_FP64) return PIC_EINVAL;
+    if (!finite_pos(p->length) || !finite_pos(p->dt) || !finite_pos(p->rho_ion)) return PIC_EINVAL;
+    if (!std::isfinite(p->qm) || !(p->qm < 0.0)) return PIC_EINVAL;
+    if (p->sort_interval < 0 || p->history < 0) return PIC_EINVAL;
+    if (p->deposit_variant < PIC_DEPOSIT_AUTO || p->deposit_variant > PIC_DEPOSIT_MATCH_PACKED) return PIC_EINVAL;
+    if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 1024 || p->block_size % 32)) return PIC_EINVAL;
+    if (p->blocks_per_sm < 0 || p->blocks_per_sm > 32) return PIC_EINVAL;
+    if (p->reserved != 0) return PIC_EINVAL;
+    return PIC_OK;
+}
+
+struct Layout {
+    size_t x[2], v[2];
+    size_t rho_q, rho_q_last, rho_f32, rho_f64;
+    size_t rho, phi, E64, E32;
+    size_t partials, dpart, hist, dev;
+    size_t s_hist, s_segtot, s_base;
+    size_t total;
+    int hist_len;
+    int nchunk, nseg, seg_len;
+    long long chunk;
+};
+
+// Device scalars of a run.
+struct DevScalars {
+    long long step;
+    unsigned err;
+    unsigned counter;
+};
+
+void sort_geometry(int64_t n, int *nchunk, long long *chunk, int *nseg, int *seg_len) {
+    long long nc = (n + 2047) / 2048;
+    if (nc < 1) nc = 1;
+    if (nc > kMaxSortChunks) nc = kMaxSortChunks;
+    long long ch = (n + nc - 1) / nc;
+    nc = (n + ch - 1) / ch;
+    int ns = 1;
+    while ((long long)ns * ns < nc) ns++;
+    *nchunk = (int)nc;
+    *chunk = ch;
+    *nseg = ns;
+    *seg_len = (int)((nc + ns - 1) / ns);
+    *nseg = (int)((nc + *seg_len - 1) / *seg_len);
+}
+
+void make_layout(const pic_params *p, Layout *L) {
+    const size_t n = (size_t)p->npart, ng = (size_t)p->ncell;
+    const size_t es = p->precision == PIC_FP64 ? 8 : 4;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+    L->x[0] = take(n * es);
+    L->v[0] = take(n * es);
+    L->x[1] = take(n * es);
+    L->v[1] = take(n * es);
+    L->rho_q = take(ng * 8);
+    L->rho_q_last = take(ng * 8);
+    L->rho_f32 = take(ng * 4);
+    L->rho_f64 = take(ng * 8);
+    L->rho = take(ng * 8);
+    L->phi = take(ng * 8);
+    L->E64 = take(ng * 8);
+    L->E32 = take(ng * 4);
+    L->partials = take((size_t)kMaxPushGrid * 2 * 8);
+    L->dpart = take((size_t)kSolveMaxBlocks * sizeof(DiagPartial));
+    L->hist_len = p->history > 0 ? p->history : kDefaultHistory;
+    L->hist = take((size_t)L->hist_len * sizeof(pic_diag_row));
+    L->dev = take(sizeof(DevScalars));
+    sort_geometry(p->npart, &L->nchunk, &L->chunk, &L->nseg, &L->seg_len);
+    L->s_hist = take((size_t)L->nchunk * ng * 4);
+    L->s_segtot = take((size_t)L->nseg * ng * 4);
+    L->s_base = take(ng * 4);
+    L->total = off;
+}
+
+int cuda_fail(cudaError_t e) {
+    if (e == cudaSuccess) return PIC_OK;
+    std::fprintf(stderr, "libpic: CUDA error %d: %s\n", (int)e, cudaGetErrorString(e));
+    return PIC_ECUDA;
+}
+
+#define PIC_CUDA(call)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_);    \
+    } while (0)
+
+}  // namespace
+
+struct pic_run {
+    pic_params p{};
+    Layout lay{};
+    int device = 0, sms = 0;
+    cudaStream_t stream = nullptr;   // the caller's
+    cudaStream_t cap = nullptr;      // private stream for graph capture
+    unsigned char *ws = nullptr;
+    int cur = 0;                     // which x/v buffer holds the state
+    int grid = 0, block = 0, variant = 0, solve_nb = 1;
+    int64_t step = 0;
+    bool ready = false, pending_push = false;
+    cudaGraphExec_t period[2] = {nullptr, nullptr};   // S steps from x parity 0/1
+    cudaGraphExec_t plain = nullptr;                  // kPlainBlock steps, no sort
+    PushConsts pc{};
+    double dx = 0, mass = 0, q_over_dx = 0, k_rho = 0, k_e = 0, k_phi = 0;
+
+    template <typename T> T *at(size_t off) const { return reinterpret_cast<T *>(ws + off); }
+    DevScalars *dev() const { return at<DevScalars>(lay.dev); }
+    size_t elem() const { return p.precision == PIC_FP64 ? 8 : 4; }
+    void *xs(int i) const { return ws + lay.x[i]; }
+    void *vs(int i) const { return ws + lay.v[i]; }
+};
+
+namespace {
+
+void destroy_graphs(pic_run *r) {
+    for (auto &g : r->period)
+        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    if (r->plain) { cudaGraphExecDestroy(r->plain); r->plain = nullptr; }
+}
+
+cudaError_t enqueue_push(pic_run *r, cudaStream_t s, bool push) {
+    const int c = r->cur;
+    if (r->p.precision == PIC_FP32_FIXED) {
+        PushArgs a;
+        a.x = (float *)r->xs(c);
+        a.v = (float *)r->vs(c);
+        a.n = r->p.npart;
+        a.E32 = r->at<float>(r->lay.E32);
+        a.rho_q = r->at<unsigned long long>(r->lay.rho_q);
+        a.partials = r->at<double>(r->lay.partials);
+        a.err = &r->dev()->err;
+        a.c = r->pc;
+        return launch_push_fixed(a, r->grid, r->block, r->variant, push, s);
+    } else if (r->p.precision == PIC_FP32_ATOMIC) {
+        PushArgsF32Atomic a;
+        a.x = (float *)r->xs(c);
+        a.v = (float *)r->vs(c);
+        a.n = r->p.npart;
+        a.E32 = r->at<float>(r->lay.E32);
+        a.rho_acc = r->at<float>(r->lay.rho_f32);
+        a.partials = r->at<double>(r->lay.partials);
+        a.err = &r->dev()->err;
+        a.c = r->pc;
+        return launch_push_f32_atomic(a, r->grid, r->block, push, s);
+    } else {
+        PushArgs64 a;
+        a.x = (double *)r->xs(c);
+        a.v = (double *)r->vs(c);
+        a.n = r->p.npart;
+        a.E64 = r->at<double>(r->lay.E64);
+        a.rho_acc = r->at<double>(r->lay.rho_f64);
+        a.partials = r->at<double>(r->lay.partials);
+        a.err = &r->dev()->err;
+        a.ng = r->p.ncell;
+        a.inv_dx = (double)r->p.ncell / r->p.length;
+        a.length = r->p.length;
+        a.qmdt = r->p.qm * r->p.dt;
+        a.dt = r->p.dt;
+        return launch_push_f64(a, r->grid, r->block, push, s);
+    }
+}
+
+cudaError_t enqueue_solve(pic_run *r, cudaStream_t s, bool after_push) {
+    SolveArgs a;
+    a.mode = r->p.precision;
+    a.rho_q = r->at<unsigned long long>(r->lay.rho_q);
+    a.rho_q_last = r->at<unsigned long long>(r->lay.rho_q_last);
+    a.rho_f32 = r->at<float>(r->lay.rho_f32);
+    a.rho_f64 = r->at<double>(r->lay.rho_f64);
+    a.rho = r->at<double>(r->lay.rho);
+    a.phi = r->at<double>(r->lay.phi);
+    a.E64 = r->at<double>(r->lay.E64);
+    a.E32 = r->at<float>(r->lay.E32);
+    a.partials = r->at<double>(r->lay.partials);
+    a.npartials = after_push ? r->grid : 0;
+    a.dpart = r->at<DiagPartial>(r->lay.dpart);
+    a.counter = &r->dev()->counter;
+    a.hist = r->at<pic_diag_row>(r->lay.hist);
+    a.hist_len = r->lay.hist_len;
+    a.dstep = &r->dev()->step;
+    a.ng = r->p.ncell;
+    a.weight_total = (long long)r->p.npart << kFixBits;
+    a.rho_ion = r->p.rho_ion;
+    a.q_over_dx = r->q_over_dx;
+    a.k_rho = r->k_rho;
+    a.k_e = r->k_e;
+    a.k_phi = r->k_phi;
+    a.dx = r->dx;
+    a.mass = r->mass;
+    return launch_solve(a, s);
+}
+
+cudaError_t enqueue_sort(pic_run *r, cudaStream_t s) {
+    const int c = r->cur;
+    cudaError_t e;
+    if (r->p.precision == PIC_FP64) {
+        SortArgs<double> a;
+        a.x = (const double *)r->xs(c); a.v = (const double *)r->vs(c);
+        a.x_out = (double *)r->xs(1 - c); a.v_out = (double *)r->vs(1 - c);
+        a.n = r->p.npart; a.ng = r->p.ncell;
+        a.inv_dx = (double)r->p.ncell / r->p.length;
+        a.nchunk = r->lay.nchunk; a.chunk = r->lay.chunk;
+        a.nseg = r->lay.nseg; a.seg_len = r->lay.seg_len;
+        a.hist = r->at<unsigned>(r->lay.s_hist);
+        a.segtot = r->at<unsigned>(r->lay.s_segtot);
+        a.base = r->at<unsigned>(r->lay.s_base);
+        a.err = &r->dev()->err;
+        e = launch_sort_f64(a, s);
+    } else {
+        SortArgs<float> a;
+        a.x = (const float *)r->xs(c); a.v = (const float *)r->vs(c);
+        a.x_out = (float *)r->xs(1 - c); a.v_out = (float *)r->vs(1 - c);
+        a.n = r->p.npart; a.ng = r->p.ncell;
+        a.inv_dx = r->pc.inv_dx;
+        a.nchunk = r->lay.nchunk; a.chunk = r->lay.chunk;
+        a.nseg = r->lay.nseg; a.seg_len = r->lay.seg_len;
+        a.hist = r->at<unsigned>(r->lay.s_hist);
+        a.segtot = r->at<unsigned>(r->lay.s_segtot);
+        a.base = r->at<unsigned>(r->lay.s_base);
+        a.err = &r->dev()->err;
+        e = launch_sort_f32(a, s);
+    }
+    if (e == cudaSuccess) r->cur = 1 - c;
+    return e;
+}
+
+// One step on stream s: [sort] + push + solve.
+cudaError_t enqueue_step(pic_run *r, cudaStream_t s, bool sort) {
+    cudaError_t e;
+    if (sort && (e = enqueue_sort(r, s)) != cudaSuccess) return e;
+    if ((e = enqueue_push(r, s, true)) != cudaSuccess) return e;
+    return enqueue_solve(r, s, true);
+}
+
+// Capture `nsteps` steps (the first with a sort if `sort_first`) starting
+// from x parity `parity` into an executable graph.
+int capture(pic_run *r, int parity, bool sort_first, int nsteps, cudaGraphExec_t *out) {
+    const int saved = r->cur;
+    r->cur = parity;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(r->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { r->cur = saved; return cuda_fail(e); }
+    cudaError_t le = cudaSuccess;
+    for (int i = 0; i < nsteps && le == cudaSuccess; i++)
+        le = enqueue_step(r, r->cap, sort_first && i == 0);
+    e = cudaStreamEndCapture(r->cap, &g);
+    r->cur = saved;
+    if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(le); }
+    if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(e); }
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    return cuda_fail(e);
+}
+
+int check_host_positions(const pic_run *r, const void *x) {
+    const int64_t n = r->p.npart;
+    if (r->p.precision == PIC_FP64) {
+        const double *xd = (const double *)x;
+        for (int64_t i = 0; i < n; i++)
+            if (!(xd[i] >= 0.0 && xd[i] < r->p.length)) return PIC_EINVAL;
+    } else {
+        const float *xf = (const float *)x;
+        const float L = r->pc.length;
+        for (int64_t i = 0; i < n; i++)
+            if (!(xf[i] >= 0.0f && xf[i] < L)) return PIC_EINVAL;
+    }
+    return PIC_OK;
+}
+
+int read_error_word(pic_run *r) {
+    unsigned err = 0;
+    PIC_CUDA(cudaMemcpyAsync(&err, &r->dev()->err, sizeof(err), cudaMemcpyDeviceToHost, r->stream));
+    PIC_CUDA(cudaStreamSynchronize(r->stream));
+    if (err & kErrTimeout) return PIC_ETIMEOUT;
+    return err ? PIC_EDEVICE : PIC_OK;
+}
+
+// Upload a state, deposit it and solve: E^step ready.
+int load_state(pic_run *r, const void *x, const void *v, int64_t step) {
+    if (!x || !v) return PIC_EINVAL;
+    int rc = check_host_positions(r, x);
+    if (rc) return rc;
+    const size_t bytes = (size_t)r->p.npart * r->elem();
+    r->cur = 0;
+    PIC_CUDA(cudaMemcpyAsync(r->xs(0), x, bytes, cudaMemcpyHostToDevice, r->stream));
+    PIC_CUDA(cudaMemcpyAsync(r->vs(0), v, bytes, cudaMemcpyHostToDevice, r->stream));
+    DevScalars ds{};
+    ds.step = step;
+    PIC_CUDA(cudaMemcpyAsync(r->dev(), &ds, sizeof(ds), cudaMemcpyHostToDevice, r->stream));
+    PIC_CUDA(cudaMemsetAsync(r->ws + r->lay.rho_q, 0, (size_t)r->p.ncell * 8, r->stream));
+    PIC_CUDA(cudaMemsetAsync(r->ws + r->lay.rho_f32, 0, (size_t)r->p.ncell * 4, r->stream));
+    PIC_CUDA(cudaMemsetAsync(r->ws + r->lay.rho_f64, 0, (size_t)r->p.ncell * 8, r->stream));
+    PIC_CUDA(cudaMemsetAsync(r->ws + r->lay.hist, 0xFF, (size_t)r->lay.hist_len * sizeof(pic_diag_row), r->stream));
+    PIC_CUDA(enqueue_push(r, r->stream, false));
+    PIC_CUDA(enqueue_solve(r, r->stream, false));
+    PIC_CUDA(cudaStreamSynchronize(r->stream));
+    r->step = step;
+    r->ready = true;
+    r->pending_push = false;
+    return read_error_word(r);
+}
+
+}  // namespace
+
+extern "C" {
+
+int pic_version(void) { return PIC_ABI_VERSION; }
+
+const char *pic_strerror(int code) {
+    switch (code) {
+        case PIC_OK: return "ok";
+        case PIC_EINVAL: return "invalid argument";
+        case PIC_ENOMEM: return "workspace too small or budget exhausted";
+        case PIC_ECUDA: return "CUDA runtime error";
+        case PIC_ETIMEOUT: return "device wait timed out";
+        case PIC_EDEVICE: return "kernel flagged bad particle data";
+        case PIC_ESTATE: return "call out of order";
+        default: return "unknown error";
+    }
+}
+
+int pic_workspace_size(const pic_params *p, size_t *bytes) {
+    int rc = validate(p);
+    if (rc) return rc;
+    if (!bytes) return PIC_EINVAL;
+    Layout L;
+    make_layout(p, &L);
+    *bytes = L.total;
+    return PIC_OK;
+}
+
+int pic_create(const pic_params *p, void *workspace, size_t workspace_bytes,
+               void *stream, pic_run **out) {
+    if (!out) return PIC_EINVAL;
+    *out = nullptr;
+    int rc = validate(p);
+    if (rc) return rc;
+    if (!workspace || ((uintptr_t)workspace % kAlign)) return PIC_EINVAL;
+    pic_run *r = new (std::nothrow) pic_run();
+    if (!r) return PIC_ENOMEM;
+    r->p = *p;
+    make_layout(p, &r->lay);
+    if (workspace_bytes < r->lay.total) { delete r; return PIC_ENOMEM; }
+    r->ws = (unsigned char *)workspace;
+    r->stream = (cudaStream_t)stream;
+    cudaError_t e = cudaGetDevice(&r->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&r->sms, cudaDevAttrMultiProcessorCount, r->device);
+    if (e == cudaSuccess) e = push_prepare_attributes(p->precision, p->ncell);
+    if (e == cudaSuccess) e = sort_prepare_attributes(p->ncell);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&r->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { delete r; return cuda_fail(e); }
+
+    // float32 constants of the push and the deposit's scale c = (float)(NG/L)
+    r->pc.ng = p->ncell;
+    r->pc.inv_dx = (float)((double)p->ncell / p->length);
+    r->pc.length = (float)p->length;
+    r->pc.qmdt = (float)(p->qm * p->dt);
+    r->pc.dt = (float)p->dt;
+    // float64 constants of the solve (Appendix A: Q0 = rho_init0 Lx / N, sign of qm)
+    r->dx = p->length / (double)p->ncell;
+    const double q0 = (p->rho_ion * p->length / (double)p->npart) * (p->qm / std::fabs(p->qm));
+    r->q_over_dx = q0 / r->dx;
+    r->mass = q0 / p->qm;
+    r->k_rho = p->rho_ion / std::ldexp((double)p->npart, kFixBits);
+    r->k_e = 0.5 * r->dx * r->k_rho / (double)p->ncell;
+    r->k_phi = -r->dx * r->dx * r->k_rho / (double)p->ncell;
+
+    // launch shape of the fused push
+    r->variant = p->deposit_variant ? p->deposit_variant : PIC_DEPOSIT_MATCH_PACKED;
+    if (p->precision != PIC_FP32_FIXED) r->variant = PIC_DEPOSIT_ATOMIC;
+    r->block = p->block_size ? p->block_size : 256;
+    int bps = push_max_blocks_per_sm(p->precision, r->variant, r->block, p->ncell);
+    if (bps < 1) { delete r; return PIC_EINVAL; }
+    if (p->blocks_per_sm && p->blocks_per_sm < bps) bps = p->blocks_per_sm;
+    long long want = (long long)r->sms * bps;
+    const long long units = p->precision == PIC_FP32_FIXED ? (p->npart + 3) / 4 : p->npart;
+    const long long need = (units + r->block - 1) / r->block;
+    if (want > need) want = need;
+    if (want > kMaxPushGrid) want = kMaxPushGrid;
+    if (want < 1) want = 1;
+    r->grid = (int)want;
+    r->solve_nb = solve_blocks(p->precision, p->ncell);
+    *out = r;
+    return PIC_OK;
+}
+
+void pic_destroy(pic_run *run) {
+    if (!run) return;
+    destroy_graphs(run);
+    if (run->cap) cudaStreamDestroy(run->cap);
+    delete run;
+}
+
+int pic_init(pic_run *run, const void *x0, const void *v0) {
+    if (!run) return PIC_EINVAL;
+    return load_state(run, x0, v0, 0);
+}
+
+int pic_set_state(pic_run *run, const void *x, const void *v, int64_t step) {
+    if (!run || step < 0) return PIC_EINVAL;
+    return load_state(run, x, v, step);
+}
+
+int pic_deposit(pic_run *run) {
+    if (!run) return PIC_EINVAL;
+    if (!run->ready) return PIC_ESTATE;
+    const size_t ng = (size_t)run->p.ncell;
+    PIC_CUDA(cudaMemsetAsync(run->ws + run->lay.rho_q, 0, ng * 8, run->stream));
+    PIC_CUDA(cudaMemsetAsync(run->ws + run->lay.rho_f32, 0, ng * 4, run->stream));
+    PIC_CUDA(cudaMemsetAsync(run->ws + run->lay.rho_f64, 0, ng * 8, run->stream));
+    PIC_CUDA(enqueue_push(run, run->stream, false));
+    return PIC_OK;
+}
+
+int pic_solve_field(pic_run *run) {
+    if (!run) return PIC_EINVAL;
+    if (!run->ready) return PIC_ESTATE;
+    PIC_CUDA(enqueue_solve(run, run->stream, run->pending_push));
+    if (run->pending_push) run->step++;
+    run->pending_push = false;
+    return PIC_OK;
+}
+
+int pic_push(pic_run *run) {
+    if (!run) return PIC_EINVAL;
+    if (!run->ready || run->pending_push) return PIC_ESTATE;
+    PIC_CUDA(enqueue_push(run, run->stream, true));
+    run->pending_push = true;
+    return PIC_OK;
+}
+
+int pic_sort(pic_run *run) {
+    if (!run) return PIC_EINVAL;
+    if (!run->ready) return PIC_ESTATE;
+    PIC_CUDA(enqueue_sort(run, run->stream));
+    return PIC_OK;
+}
+
+int pic_step_n(pic_run *run, int64_t n) {
+    if (!run || n < 0) return PIC_EINVAL;
+    if (!run->ready || run->pending_push) return PIC_ESTATE;
+    const int64_t S = run->p.sort_interval;
+    while (n > 0) {
+        const bool sort_due = S > 0 && run->step > 0 && run->step % S == 0;
+        if (sort_due && n >= S) {
+            cudaGraphExec_t &g = run->period[run->cur];
+            if (!g) {
+                int rc = capture(run, run->cur, true, (int)S, &g);
+                if (rc) return rc;
+            }
+            PIC_CUDA(cudaGraphLaunch(g, run->stream));
+            run->cur = 1 - run->cur;
+            run->step += S;
+            n -= S;
+        } else if (S == 0 && n >= kPlainBlock) {
+            if (!run->plain) {
+                int rc = capture(run, run->cur, false, kPlainBlock, &run->plain);
+                if (rc) return rc;
+            }
+            PIC_CUDA(cudaGraphLaunch(run->plain, run->stream));
+            run->step += kPlainBlock;
+            n -= kPlainBlock;
+        } else {
+            PIC_CUDA(enqueue_step(run, run->stream, sort_due));
+            run->step += 1;
+            n -= 1;
+        }
+    }
+    return PIC_OK;
+}
+
+int pic_sync(pic_run *run) {
+    if (!run) return PIC_EINVAL;
+    PIC_CUDA(cudaStreamSynchronize(run->stream));
+    return read_error_word(run);
+}
+
+int64_t pic_step_count(const pic_run *run) { return run ? run->step : -1; }
+
+int pic_diagnostics(pic_run *run, int64_t first, int32_t count, pic_diag_row *rows) {
+    if (!run || !rows || count < 0 || first < 0) return PIC_EINVAL;
+    if (!run->ready) return PIC_ESTATE;
+    const int64_t H = run->lay.hist_len;
+    const int64_t last = first + count - 1;
+    if (count == 0) return PIC_OK;
+    if (last > run->step || first < run->step - H + 1) return PIC_EINVAL;
+    const pic_diag_row *hist = run->at<pic_diag_row>(run->lay.hist);
+    int64_t done = 0;
+    while (done < count) {
+        const int64_t slot = (first + done) % H;
+        int64_t len = count - done;
+        if (slot + len > H) len = H - slot;
+        PIC_CUDA(cudaMemcpyAsync(rows + done, hist + slot, (size_t)len * sizeof(pic_diag_row),
+                                 cudaMemcpyDeviceToHost, run->stream));
+        done += len;
+    }
+    PIC_CUDA(cudaStreamSynchronize(run->stream));
+    return read_error_word(run);
+}
+
+int pic_get_state(pic_run *run, void *x, void *v) {
+    if (!run) return PIC_EINVAL;
+    if (!run->ready) return PIC_ESTATE;
+    const size_t bytes = (size_t)run->p.npart * run->elem();
+    if (x) PIC_CUDA(cudaMemcpyAsync(x, run->xs(run->cur), bytes, cudaMemcpyDeviceToHost, run->stream));
+    if (v) PIC_CUDA(cudaMemcpyAsync(v, run->vs(run->cur), bytes, cudaMemcpyDeviceToHost, run->stream));
+    PIC_CUDA(cudaStreamSynchronize(run->stream));
+    return read_error_word(run);
+}
+
+int pic_get_field(pic_run *run, double *rho, double *phi, double *E, int64_t *rho_q) {
+    if (!run) return PIC_EINVAL;
+    if (!run->ready) return PIC_ESTATE;
+    const size_t ng = (size_t)run->p.ncell;
+    if (rho) PIC_CUDA(cudaMemcpyAsync(rho, run->ws + run->lay.rho, ng * 8, cudaMemcpyDeviceToHost, run->stream));
+    if (phi) PIC_CUDA(cudaMemcpyAsync(phi, run->ws + run->lay.phi, ng * 8, cudaMemcpyDeviceToHost, run->stream));
+    if (E) PIC_CUDA(cudaMemcpyAsync(E, run->ws + run->lay.E64, ng * 8, cudaMemcpyDeviceToHost, run->stream));
+    if (rho_q) {
+        if (run->p.precision == PIC_FP32_FIXED)
+            PIC_CUDA(cudaMemcpyAsync(rho_q, run->ws + run->lay.rho_q_last, ng * 8, cudaMemcpyDeviceToHost, run->stream));
+        else
+            std::memset(rho_q, 0, ng * 8);
+    }
+    PIC_CUDA(cudaStreamSynchronize(run->stream));
+    return read_error_word(run);
+}
+
+int pic_device_arrays(pic_run *run, void **x, void **v, void **E32) {
+    if (!run) return PIC_EINVAL;
+    if (x) *x = run->xs(run->cur);
+    if (v) *v = run->vs(run->cur);
+    if (E32) *E32 = run->ws + run->lay.E32;
+    return PIC_OK;
+}
+
+int pic_launch_shape(const pic_run *run, int32_t *grid, int32_t *block, int32_t *variant) {
+    if (!run) return PIC_EINVAL;
+    if (grid) *grid = run->grid;
+    if (block) *block = run->block;
+    if (variant) *variant = run->variant;
+    return PIC_OK;
+}
+
+}  // extern "C"

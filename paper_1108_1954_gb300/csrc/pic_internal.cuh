@@ -1,0 +1,139 @@
+// pic_internal.cuh -- kernel argument blocks and launcher declarations shared
+// by the translation units of libpic (not part of the public ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/pic.h"
+
+namespace pic {
+
+// Fixed-point deposit: each particle adds exactly 2^24 to the density sum.
+constexpr int kFixBits = 24;
+constexpr uint32_t kFixOne = 1u << kFixBits;
+
+// Bits of the device error word.
+enum : uint32_t {
+    kErrPosition = 1u,   // a position outside [0, L) or not finite
+    kErrTimeout = 2u,    // a bounded device wait ran out
+    kErrSortKey = 4u,    // a sort key outside the grid
+};
+
+// Float32 constants of the push, formed once on the host.
+struct PushConsts {
+    int ng;          // NG
+    float inv_dx;    // (float)(NG / L): the deposit's scale c
+    float length;    // (float)L
+    float qmdt;      // (float)(qm * dt)
+    float dt;        // (float)dt
+};
+
+// Fused push + fixed-point deposit (or deposit alone when push == false).
+struct PushArgs {
+    float *x, *v;                 // N each, 16-byte aligned
+    long long n;                  // N
+    const float *E32;             // field at the nodes, float32 [NG]
+    unsigned long long *rho_q;    // fixed-point density accumulator [NG]
+    double *partials;             // per-block [sum v_old v_new, sum v_new]
+    unsigned int *err;            // device error word
+    PushConsts c;
+};
+
+// Float64 push (PIC_FP64) and float32 push with float32 atomic deposit.
+struct PushArgs64 {
+    double *x, *v;
+    long long n;
+    const double *E64;
+    double *rho_acc;              // sum of weights per node [NG]
+    double *partials;
+    unsigned int *err;
+    int ng;
+    double inv_dx, length, qmdt, dt;
+};
+
+struct PushArgsF32Atomic {
+    float *x, *v;
+    long long n;
+    const float *E32;
+    float *rho_acc;               // sum of float32 weights per node [NG]
+    double *partials;
+    unsigned int *err;
+    PushConsts c;
+};
+
+// Per-block share of the step diagnostics, reduced by the solve's last block.
+struct DiagPartial {
+    double fe, ke, mom, charge;
+    unsigned long long cq;
+    double md[2 * PIC_NMODES];     // mode sums re, im
+};
+
+// Field solve (fixed point: up to kSolveMaxBlocks blocks; float modes: 1).
+struct SolveArgs {
+    int mode;                     // PIC_FP32_FIXED / PIC_FP32_ATOMIC / PIC_FP64
+    unsigned long long *rho_q;    // FIXED: accumulator (read, then zeroed)
+    unsigned long long *rho_q_last; // FIXED: copy of the consumed sums
+    float *rho_f32;               // FP32_ATOMIC accumulator
+    double *rho_f64;              // FP64 accumulator
+    double *rho, *phi, *E64;      // outputs [NG]
+    float *E32;                   // output copy for the gather [NG]
+    const double *partials;       // per-block sums of the push that ran
+    int npartials;                // 0: no push ran since the last solve
+    DiagPartial *dpart;           // [kSolveMaxBlocks]
+    unsigned *counter;            // last-block ticket (0 between launches)
+    pic_diag_row *hist;           // history ring
+    int hist_len;
+    long long *dstep;             // device step counter
+    int ng;
+    long long weight_total;       // N 2^24
+    double rho_ion;
+    double q_over_dx;             // Q0/dx = -rho_ion NG / N (float modes)
+    double k_rho;                 // rho_ion / (N 2^24)
+    double k_e;                   // (dx/2) k_rho / NG
+    double k_phi;                 // -dx^2 k_rho / NG
+    double dx;
+    double mass;                  // particle mass m = Q0/qm
+};
+
+// Counting sort by cell.
+template <typename T>
+struct SortArgs {
+    const T *x, *v;               // source
+    T *x_out, *v_out;             // destination
+    long long n;
+    int ng;
+    T inv_dx;                     // NG / L in the particle precision
+    int nchunk;                   // blocks of the count/scatter passes
+    long long chunk;              // particles per block
+    int nseg;                     // chunk segments of the column scan
+    int seg_len;                  // chunks per segment
+    unsigned int *hist;           // [nchunk][NG] counts, then offsets
+    unsigned int *segtot;         // [nseg][NG] segment totals, then offsets
+    unsigned int *base;           // [NG] first slot of each cell
+    unsigned int *err;
+};
+
+// Launchers (each returns the launch's cudaError_t).
+cudaError_t launch_push_fixed(const PushArgs &a, int grid, int block,
+                              int variant, bool push, cudaStream_t s);
+cudaError_t launch_push_f32_atomic(const PushArgsF32Atomic &a, int grid,
+                                   int block, bool push, cudaStream_t s);
+cudaError_t launch_push_f64(const PushArgs64 &a, int grid, int block,
+                            bool push, cudaStream_t s);
+size_t push_smem_bytes(int mode, int ng);
+cudaError_t push_prepare_attributes(int mode, int ng);
+int push_max_blocks_per_sm(int mode, int variant, int block, int ng);
+
+cudaError_t launch_solve(const SolveArgs &a, cudaStream_t s);
+constexpr int kSolveThreads = 1024;
+constexpr int kSolveMaxBlocks = 32;
+int solve_blocks(int mode, int ng);
+
+cudaError_t launch_sort_f32(const SortArgs<float> &a, cudaStream_t s);
+cudaError_t launch_sort_f64(const SortArgs<double> &a, cudaStream_t s);
+cudaError_t sort_prepare_attributes(int ng);
+constexpr int kSortThreads = 256;
+
+}  // namespace pic

@@ -1,0 +1,187 @@
+// sort.cu -- periodic counting sort of the particles by cell.
+//
+// Not a step of the paper's method: it reorders the particle arrays so that
+// the particles a warp handles share few cells, which makes the fused push's
+// field reads broadcasts and lets its deposit aggregate equal nodes before the
+// shared-memory atomics.  It changes no physical quantity.
+//
+// Four passes, all deterministic and stable (particles of one cell keep their
+// relative order):
+//   count    block b counts the cells of its contiguous chunk -> hist[b][g]
+//   colscan  per (segment of chunks, cell): exclusive prefix over the chunks
+//            of the segment, in place, and the segment total
+//   base     per cell: exclusive prefix over segments, in place; then the
+//            exclusive prefix of the cell totals over cells -> base[g]
+//   scatter  block b walks its chunk in order, 256 particles at a time; the
+//            warps take their slots from the per-cell cursor one after the
+//            other, so the order within a cell is the original order.
+// The destination index is bounds-checked; a violation sets the device error
+// word instead of writing.
+#include "pic_internal.cuh"
+
+namespace pic {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr unsigned kNoKey = 0xffffffffu;
+
+template <typename T>
+__device__ __forceinline__ unsigned cell_key(T x, T inv_dx, int ng) {
+    T u = x * inv_dx;
+    u = u > (T)0 ? u : (T)0;                  // also maps NaN to 0
+    const T top = (T)(ng - 1);
+    u = u < top ? u : top;
+    return (unsigned)u;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSortThreads) sort_count_kernel(SortArgs<T> a) {
+    extern __shared__ unsigned sh_count[];
+    const int ng = a.ng;
+    for (int g = threadIdx.x; g < ng; g += blockDim.x) sh_count[g] = 0u;
+    __syncthreads();
+    const long long start = (long long)blockIdx.x * a.chunk;
+    const long long end = min(a.n, start + a.chunk);
+    const int lane = threadIdx.x & 31;
+    for (long long i0 = start; i0 < end; i0 += blockDim.x) {
+        const long long i = i0 + threadIdx.x;
+        const bool valid = i < end;
+        const unsigned key = valid ? cell_key(a.x[i], a.inv_dx, ng) : kNoKey;
+        const unsigned peers = __match_any_sync(kFull, key);
+        if (valid && lane == __ffs(peers) - 1) atomicAdd(&sh_count[key], (unsigned)__popc(peers));
+    }
+    __syncthreads();
+    unsigned *row = a.hist + (size_t)blockIdx.x * ng;
+    for (int g = threadIdx.x; g < ng; g += blockDim.x) row[g] = sh_count[g];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) sort_colscan_kernel(SortArgs<T> a) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= a.ng) return;
+    const int seg = blockIdx.y;
+    const int b0 = seg * a.seg_len, b1 = min(a.nchunk, b0 + a.seg_len);
+    unsigned run = 0;
+    for (int b = b0; b < b1; b++) {
+        unsigned *p = a.hist + (size_t)b * a.ng + g;
+        const unsigned c = *p;
+        *p = run;
+        run += c;
+    }
+    a.segtot[(size_t)seg * a.ng + g] = run;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) sort_base_kernel(SortArgs<T> a) {
+    __shared__ unsigned wt[32];
+    const int ng = a.ng, T_ = blockDim.x, t = threadIdx.x;
+    const int k = (ng + T_ - 1) / T_;
+    const int g0 = t * k;
+    unsigned local = 0;
+    for (int j = 0; j < k; j++) {
+        const int g = g0 + j;
+        if (g >= ng) break;
+        unsigned run = 0;
+        for (int s = 0; s < a.nseg; s++) {
+            unsigned *p = a.segtot + (size_t)s * ng + g;
+            const unsigned c = *p;
+            *p = run;
+            run += c;
+        }
+        a.base[g] = run;   // cell total for now
+        local += run;
+    }
+    // exclusive prefix of thread sums
+    const int lane = t & 31, w = t >> 5, nw = T_ >> 5;
+    unsigned inc = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned u = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += u;
+    }
+    if (lane == 31) wt[w] = inc;
+    __syncthreads();
+    unsigned off = 0;
+    for (int i = 0; i < w && i < nw; i++) off += wt[i];
+    unsigned run = off + inc - local;
+    for (int j = 0; j < k; j++) {
+        const int g = g0 + j;
+        if (g >= ng) break;
+        const unsigned c = a.base[g];
+        a.base[g] = run;
+        run += c;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(SortArgs<T> a) {
+    extern __shared__ unsigned cursor[];
+    const int ng = a.ng;
+    const int seg = blockIdx.x / a.seg_len;
+    const unsigned *row = a.hist + (size_t)blockIdx.x * ng;
+    const unsigned *srow = a.segtot + (size_t)seg * ng;
+    for (int g = threadIdx.x; g < ng; g += blockDim.x) cursor[g] = a.base[g] + srow[g] + row[g];
+    __syncthreads();
+    const long long start = (long long)blockIdx.x * a.chunk;
+    const long long end = min(a.n, start + a.chunk);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    for (long long i0 = start; i0 < end; i0 += blockDim.x) {
+        const long long i = i0 + threadIdx.x;
+        const bool valid = i < end;
+        const T x = valid ? a.x[i] : (T)0;
+        const T v = valid ? a.v[i] : (T)0;
+        const unsigned key = valid ? cell_key(x, a.inv_dx, ng) : kNoKey;
+        const unsigned peers = __match_any_sync(kFull, key);
+        const int leader = __ffs(peers) - 1;
+        unsigned base = 0;
+        for (int w = 0; w < nwarp; w++) {
+            if (w == warp && valid && lane == leader) {
+                base = cursor[key];
+                cursor[key] = base + (unsigned)__popc(peers);
+            }
+            __syncthreads();
+        }
+        base = __shfl_sync(kFull, base, leader);
+        if (valid) {
+            const unsigned long long dst = (unsigned long long)base + __popc(peers & lt);
+            if (dst < (unsigned long long)a.n) {
+                a.x_out[dst] = x;
+                a.v_out[dst] = v;
+            } else {
+                atomicOr(a.err, kErrSortKey);
+            }
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_sort_t(const SortArgs<T> &a, cudaStream_t s) {
+    const size_t smem = (size_t)a.ng * sizeof(unsigned);
+    sort_count_kernel<T><<<a.nchunk, kSortThreads, smem, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dim3 cg((a.ng + 255) / 256, a.nseg);
+    sort_colscan_kernel<T><<<cg, 256, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    sort_base_kernel<T><<<1, 1024, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    sort_scatter_kernel<T><<<a.nchunk, kSortThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t sort_prepare_attributes(int ng) {
+    (void)ng;
+    const int bytes = PIC_NCELL_MAX * (int)sizeof(unsigned);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(&sort_count_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
+    if ((e = cudaFuncSetAttribute(&sort_scatter_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
+    if ((e = cudaFuncSetAttribute(&sort_count_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
+    return cudaFuncSetAttribute(&sort_scatter_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+cudaError_t launch_sort_f32(const SortArgs<float> &a, cudaStream_t s) { return launch_sort_t(a, s); }
+cudaError_t launch_sort_f64(const SortArgs<double> &a, cudaStream_t s) { return launch_sort_t(a, s); }
+
+}  // namespace pic

@@ -9,3 +9,7 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line(
         "markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
+    # Build the CUDA library (nvcc cross-compiles without a GPU) and the C
+    # oracle before collection, so every test module can import them.
+    import __graft_entry__
+    __graft_entry__.build()

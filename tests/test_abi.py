@@ -1,0 +1,77 @@
+"""The C-ABI library loads, exports every function include/pic.h declares, and
+rejects bad parameters -- host-side checks that need no GPU."""
+import ctypes as C
+import math
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pic():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1108_1954_gb300 as pic
+    return pic
+
+
+def test_library_exports_every_header_function(pic):
+    names = pic.header_functions(os.path.join(ROOT, "include", "pic.h"))
+    assert len(names) >= 19
+    lib = C.CDLL(pic.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_version_and_error_text(pic):
+    assert pic._lib.pic_version() == 1
+    assert pic.strerror(pic.PIC_EINVAL) == "invalid argument"
+    assert pic.strerror(pic.PIC_EDEVICE).startswith("kernel flagged")
+    assert pic.strerror(12345) == "unknown error"
+
+
+def _params(pic, **kw):
+    base = dict(npart=1000, ncell=64, length=4 * math.pi, dt=0.1)
+    base.update(kw)
+    return pic.Params(**base)
+
+
+def test_workspace_size_scales_with_particles(pic):
+    a = pic.workspace_size(_params(pic, npart=1 << 20))
+    b = pic.workspace_size(_params(pic, npart=1 << 21))
+    # four float32 particle arrays (state + sort buffer), 16 B per particle
+    assert 16 * (1 << 20) <= b - a <= 16 * (1 << 20) + (1 << 20)
+    d = pic.workspace_size(_params(pic, npart=1 << 20, precision=pic.PIC_FP64))
+    assert d - a >= 16 * (1 << 20)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(npart=0), dict(ncell=0), dict(ncell=8193), dict(qm=1.0), dict(qm=0.0),
+    dict(dt=0.0), dict(length=float("nan")), dict(length=-1.0),
+    dict(rho_ion=0.0), dict(block_size=33), dict(block_size=2048),
+    dict(deposit_variant=9), dict(precision=7), dict(sort_interval=-1),
+    dict(npart=1 << 33)])
+def test_invalid_parameters_rejected(pic, bad):
+    with pytest.raises(pic.PicError) as e:
+        pic.workspace_size(_params(pic, **bad))
+    assert e.value.code == pic.PIC_EINVAL
+
+
+def test_create_rejects_missing_or_small_workspace(pic):
+    p = _params(pic).c()
+    h = C.c_void_p()
+    assert pic._lib.pic_create(C.byref(p), None, 0, None, C.byref(h)) == pic.PIC_EINVAL
+    # misaligned workspace pointer
+    assert pic._lib.pic_create(C.byref(p), C.c_void_p(16), 1 << 30, None,
+                               C.byref(h)) == pic.PIC_EINVAL
+    assert pic._lib.pic_create(None, C.c_void_p(256), 1, None, C.byref(h)) == pic.PIC_EINVAL
+
+
+def test_calls_on_null_run_are_rejected(pic):
+    lib = pic._lib
+    assert lib.pic_push(None) == pic.PIC_EINVAL
+    assert lib.pic_step_n(None, 1) == pic.PIC_EINVAL
+    assert lib.pic_solve_field(None) == pic.PIC_EINVAL
+    assert lib.pic_step_count(None) == -1
