@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--variant", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--bps", type=int, default=0)
+    ap.add_argument("--unroll", type=int, default=0)
+    ap.add_argument("--no-tune", action="store_true")
     return ap.parse_args()
 
 
@@ -157,10 +159,12 @@ def time_ours(args, w, x32, v32):
     n, S = w["npart"], w["sort_interval"]
     params = pic.Params(npart=n, ncell=w["ncell"], length=w["length"], dt=w["dt"],
                         sort_interval=S, history=8192, deposit_variant=args.variant,
-                        block_size=args.block, blocks_per_sm=args.bps)
+                        block_size=args.block, blocks_per_sm=args.bps, unroll=args.unroll)
     run = pic.Run(params, device="cuda")
     stream = run.stream
     run.init(x32, v32)
+    if not args.no_tune and not args.variant:
+        run.autotune(reps=3)
     launches = {"n": 0}
 
     def one_step(ev=None):
@@ -199,6 +203,7 @@ def time_ours(args, w, x32, v32):
     push_ms = [a.elapsed_time(b) for a, b in evs]
     run.sync()
     grid, block, variant = run.launch_shape()
+    unroll = run.p.unroll
     diag = run.diagnostics(run.step - 1, 1)[0]
     res = dict(total_ms=total_ms, push_ms=push_ms, clocks=ck, launches=launches["n"],
                grid=grid, block=block, variant=variant, steps=K,
@@ -220,9 +225,11 @@ def time_e2e(args, w, x32, v32):
     params = pic.Params(npart=n, ncell=w["ncell"], length=w["length"], dt=w["dt"],
                         sort_interval=w["sort_interval"], history=max(8192, K + 1),
                         deposit_variant=args.variant, block_size=args.block,
-                        blocks_per_sm=args.bps)
+                        blocks_per_sm=args.bps, unroll=args.unroll)
     run = pic.Run(params, device="cuda")
-    run.init(xh, vh)                      # warm: graph capture, first touch
+    run.init(xh, vh)                      # warm: autotune, graph capture, first touch
+    if not args.no_tune and not args.variant:
+        run.autotune(reps=3)
     run.step_n(w["sort_interval"] + 1)
     run.sync()
     torch.cuda.synchronize()

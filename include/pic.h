@@ -71,6 +71,8 @@ extern "C" {
 #define PIC_DEPOSIT_MATCH 2  /* warp groups of equal cell (match + reduce)   */
 #define PIC_DEPOSIT_PACKED 3 /* count and weight packed in one atomic        */
 #define PIC_DEPOSIT_MATCH_PACKED 4 /* warp groups, one packed atomic each   */
+#define PIC_DEPOSIT_QUAD 5         /* runs within a thread's 4 particles,
+                                      two atomics per run                  */
 
 #define PIC_NCELL_MAX 8192  /* largest NG (the per-block density tile)       */
 #define PIC_NMODES 8        /* Fourier modes recorded per step               */
@@ -87,9 +89,11 @@ typedef struct pic_params {
     int32_t sort_interval; /* counting sort by cell every S steps (0 = never)  */
     int32_t history;       /* rows of the device diagnostics ring (>= 1)       */
     int32_t deposit_variant; /* PIC_DEPOSIT_*                                 */
-    int32_t block_size;    /* threads per block of the fused push (0 = auto)   */
+    int32_t block_size;    /* threads per block of the fused push (0 = auto;
+                              at most 512 in PIC_FP32_FIXED, else 1024)       */
     int32_t blocks_per_sm; /* resident blocks per SM of the fused push (0=auto)*/
-    int32_t reserved;      /* must be 0                                       */
+    int32_t unroll;        /* float4 groups per thread per iteration of the
+                              fused push: 1, 2, 4 (0 = auto)                 */
 } pic_params;
 
 /* One row of the per-step diagnostics (all float64 on the device). */
@@ -192,6 +196,22 @@ int pic_device_arrays(pic_run *run, void **x, void **v, void **E32);
 /* The launch shape the run uses for its fused push. */
 int pic_launch_shape(const pic_run *run, int32_t *grid, int32_t *block,
                      int32_t *variant);
+
+/* One timed candidate of pic_autotune. */
+typedef struct pic_tune_entry {
+    int32_t variant, block, unroll, grid;
+    float ms;                 /* median CUDA-event time of one fused push     */
+} pic_tune_entry;
+
+/* Autotune the fused push (PIC_FP32_FIXED): time every candidate shape
+ * (deposit variant x block size x unroll) for `reps` pushes on a copy of the
+ * current particles (the sort buffers and a scratch density accumulator; the
+ * run's state is untouched), then adopt the fastest.  Writes up to
+ * max_results entries to results (may be NULL) and their count to *nresults.
+ * Synchronises.  PIC_ESTATE before pic_init or between pic_push and
+ * pic_solve_field. */
+int pic_autotune(pic_run *run, int32_t reps, pic_tune_entry *results,
+                 int32_t max_results, int32_t *nresults);
 
 #ifdef __cplusplus
 }

@@ -30,14 +30,15 @@ PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA = 0, -1, -2, -3
 PIC_ETIMEOUT, PIC_EDEVICE, PIC_ESTATE = -4, -5, -6
 PIC_FP32_FIXED, PIC_FP32_ATOMIC, PIC_FP64 = 0, 1, 2
 PIC_DEPOSIT_AUTO, PIC_DEPOSIT_ATOMIC, PIC_DEPOSIT_MATCH = 0, 1, 2
-PIC_DEPOSIT_PACKED, PIC_DEPOSIT_MATCH_PACKED = 3, 4
+PIC_DEPOSIT_PACKED, PIC_DEPOSIT_MATCH_PACKED, PIC_DEPOSIT_QUAD = 3, 4, 5
 PIC_NCELL_MAX = 8192
 PIC_NMODES = 8
 FIX_BITS = 24
 
 VARIANT_NAMES = {PIC_DEPOSIT_ATOMIC: "atomic", PIC_DEPOSIT_MATCH: "match",
                  PIC_DEPOSIT_PACKED: "packed",
-                 PIC_DEPOSIT_MATCH_PACKED: "match_packed"}
+                 PIC_DEPOSIT_MATCH_PACKED: "match_packed",
+                 PIC_DEPOSIT_QUAD: "quad"}
 
 
 class CParams(C.Structure):
@@ -47,7 +48,7 @@ class CParams(C.Structure):
                 ("rho_ion", C.c_double), ("sort_interval", C.c_int32),
                 ("history", C.c_int32), ("deposit_variant", C.c_int32),
                 ("block_size", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("unroll", C.c_int32)]
 
 
 class CDiagRow(C.Structure):
@@ -56,6 +57,9 @@ class CDiagRow(C.Structure):
                 ("charge", C.c_double), ("charge_q", C.c_int64),
                 ("mode", C.c_double * PIC_NMODES)]
 
+
+TUNE_DTYPE = np.dtype([("variant", np.int32), ("block", np.int32),
+                       ("unroll", np.int32), ("grid", np.int32), ("ms", np.float32)])
 
 DIAG_DTYPE = np.dtype([("step", np.int64), ("kinetic", np.float64),
                        ("momentum", np.float64), ("field", np.float64),
@@ -87,6 +91,7 @@ _SIG = {
                                     C.POINTER(_VP)]),
     "pic_launch_shape": (C.c_int, [_VP, C.POINTER(C.c_int32),
                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "pic_autotune": (C.c_int, [_VP, C.c_int32, _VP, C.c_int32, C.POINTER(C.c_int32)]),
 }
 for _name, (_res, _args) in _SIG.items():
     _fn = getattr(_lib, _name)
@@ -134,13 +139,15 @@ class Params:
     deposit_variant: int = PIC_DEPOSIT_AUTO
     block_size: int = 0
     blocks_per_sm: int = 0
+    unroll: int = 0
 
     def c(self) -> CParams:
         return CParams(int(self.npart), int(self.ncell), int(self.precision),
                        float(self.length), float(self.dt), float(self.qm),
                        float(self.rho_ion), int(self.sort_interval),
                        int(self.history), int(self.deposit_variant),
-                       int(self.block_size), int(self.blocks_per_sm), 0)
+                       int(self.block_size), int(self.blocks_per_sm),
+                       int(self.unroll))
 
     @property
     def dtype(self):
@@ -261,6 +268,15 @@ class Run:
             return self.workspace[off:off + count * size].view(dt)
         return (view(x.value, n, tdt, es), view(v.value, n, tdt, es),
                 view(e.value, self.p.ncell, torch.float32, 4))
+
+    def autotune(self, reps: int = 5) -> np.ndarray:
+        """Time the candidate push shapes on a copy of the state and adopt
+        the fastest; returns the timings."""
+        out = np.zeros(64, dtype=TUNE_DTYPE)
+        n = C.c_int32(0)
+        _check(_lib.pic_autotune(self._h, int(reps), _VP(out.ctypes.data), 64, C.byref(n)),
+               "pic_autotune")
+        return out[:n.value]
 
     def launch_shape(self):
         g, b, v = C.c_int32(), C.c_int32(), C.c_int32()

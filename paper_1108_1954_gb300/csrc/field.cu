@@ -36,39 +36,10 @@
 // per-block float64 sums, reduced in a fixed order.
 #include <math.h>
 
-#include "pic_internal.cuh"
+#include "field_ops.cuh"
 
 namespace pic {
 namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
-typedef __int128 i128;
-
-__device__ __forceinline__ i128 shfl_up_i128(i128 v, int o) {
-    long long lo = (long long)(unsigned long long)v;
-    long long hi = (long long)(v >> 64);
-    lo = __shfl_up_sync(kFull, lo, o);
-    hi = __shfl_up_sync(kFull, hi, o);
-    return (i128)(((unsigned __int128)(unsigned long long)hi << 64) |
-                  (unsigned long long)lo);
-}
-
-__device__ __forceinline__ i128 shfl_down_i128(i128 v, int o) {
-    long long lo = (long long)(unsigned long long)v;
-    long long hi = (long long)(v >> 64);
-    lo = __shfl_down_sync(kFull, lo, o);
-    hi = __shfl_down_sync(kFull, hi, o);
-    return (i128)(((unsigned __int128)(unsigned long long)hi << 64) |
-                  (unsigned long long)lo);
-}
-
-__device__ __forceinline__ double i128_to_f64(i128 v) {
-    const long long hi = (long long)(v >> 64);
-    const unsigned long long lo = (unsigned long long)v;
-    if ((hi == 0 && (long long)lo >= 0) || (hi == -1 && (long long)lo < 0))
-        return (double)(long long)lo;
-    return fma((double)hi, 0x1p64, (double)lo);
-}
 
 // Inclusive scan of one i128 per thread over the block; returns the inclusive
 // value and the block total.  sh must hold 33 entries.
@@ -124,25 +95,6 @@ __device__ void block_sum_t(T (&v)[K], T *sh /*[32*K]*/) {
     __syncthreads();
 }
 
-// Per-node diagnostics contribution of node g with field E (float64) and
-// its float32 copy, added to the block's accumulators.
-struct NodeDiag {
-    double fe;
-    float re[PIC_NMODES], im[PIC_NMODES];
-};
-
-__device__ __forceinline__ void node_diag(NodeDiag &d, int g, int ng, double E, float E32) {
-    d.fe = fma(E, E, d.fe);
-#pragma unroll
-    for (int m = 1; m <= PIC_NMODES; m++) {
-        const int ph = (int)(((long long)m * g) % ng);
-        float sn, cs;
-        sincospif(2.0f * (float)ph / (float)ng, &sn, &cs);
-        d.re[m - 1] = fmaf(E32, cs, d.re[m - 1]);
-        d.im[m - 1] = fmaf(-E32, sn, d.im[m - 1]);
-    }
-}
-
 // The block's share of the diagnostics, written to a.dpart[blockIdx.x]; the
 // push's per-block sums are split over the solve blocks.
 __device__ void write_block_partials(const SolveArgs &a, NodeDiag &d, double charge,
@@ -162,19 +114,22 @@ __device__ void write_block_partials(const SolveArgs &a, NodeDiag &d, double cha
     block_sum_t<2 * PIC_NMODES, float>(md, shf);
     if (threadIdx.x == 0) {
         DiagPartial &p = a.dpart[blockIdx.x];
-        p.fe = kv[0];
-        p.ke = kv[1];
-        p.mom = kv[2];
-        p.charge = charge;
+        p.v[kDiagFE] = kv[0];
+        p.v[kDiagKE] = kv[1];
+        p.v[kDiagMom] = kv[2];
+        p.v[kDiagCharge] = charge;
         p.cq = cq;
-        for (int m = 0; m < 2 * PIC_NMODES; m++) p.md[m] = (double)md[m];
+        for (int m = 0; m < 2 * PIC_NMODES; m++) p.v[kDiagModes + m] = (double)md[m];
     }
 }
 
 // Last block: reduce the per-block partials in a fixed order, write the
-// history rows, clear the accumulator, advance the step counter.
+// history rows, clear the accumulator, advance the step counter.  Field f of
+// the partials is summed over the blocks by thread f.
 __device__ void finalize(const SolveArgs &a, long long step) {
     __shared__ unsigned ticket;
+    __shared__ double tot[kDiagFields];
+    __shared__ unsigned long long tot_cq;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) ticket = atomicAdd(a.counter, 1u);
@@ -188,20 +143,23 @@ __device__ void finalize(const SolveArgs &a, long long step) {
         else if (a.mode == PIC_FP32_ATOMIC) a.rho_f32[g] = 0.0f;
         else a.rho_f64[g] = 0.0;
     }
+    const int f = threadIdx.x;
+    if (f < kDiagFields) {
+        double acc = 0.0;
+        for (int b = 0; b < (int)gridDim.x; b++) acc += __ldcg(&a.dpart[b].v[f]);
+        tot[f] = acc;
+    } else if (f == kDiagFields) {
+        unsigned long long acc = 0;
+        for (int b = 0; b < (int)gridDim.x; b++) acc += __ldcg(&a.dpart[b].cq);
+        tot_cq = acc;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        double fe = 0, ke = 0, mom = 0, charge = 0, md[2 * PIC_NMODES];
-        unsigned long long cq = 0;
-        for (int m = 0; m < 2 * PIC_NMODES; m++) md[m] = 0.0;
-        for (int b = 0; b < (int)gridDim.x; b++) {
-            volatile DiagPartial &p = a.dpart[b];
-            fe += p.fe; ke += p.ke; mom += p.mom; charge += p.charge; cq += p.cq;
-            for (int m = 0; m < 2 * PIC_NMODES; m++) md[m] += p.md[m];
-        }
         long long n = step;
         if (a.npartials > 0) {
             pic_diag_row *row = &a.hist[n % a.hist_len];
-            row->kinetic = 0.5 * a.mass * ke;
-            row->momentum = a.mass * mom;
+            row->kinetic = 0.5 * a.mass * tot[kDiagKE];
+            row->momentum = a.mass * tot[kDiagMom];
             n = step + 1;
             *a.dstep = n;
         }
@@ -210,11 +168,11 @@ __device__ void finalize(const SolveArgs &a, long long step) {
         row->step = n;
         row->kinetic = qnan;
         row->momentum = qnan;
-        row->field = 0.5 * a.dx * fe;
-        row->charge = charge;
-        row->charge_q = (long long)cq;
+        row->field = 0.5 * a.dx * tot[kDiagFE];
+        row->charge = tot[kDiagCharge];
+        row->charge_q = (long long)tot_cq;
         for (int m = 0; m < PIC_NMODES; m++) {
-            const double re = md[2 * m], im = md[2 * m + 1];
+            const double re = tot[kDiagModes + 2 * m], im = tot[kDiagModes + 2 * m + 1];
             row->mode[m] = 2.0 * sqrt(re * re + im * im) / (double)ng;
         }
         *a.counter = 0u;
@@ -236,8 +194,9 @@ __global__ void __launch_bounds__(256) pic_solve_fixed_kernel(SolveArgs a) {
     //   A0 = sum_{k<b0} R_k, A1 = sum_{k<b0} (b0-k) R_k   (prefixes to b0)
     //   SP = sum_k (NG-k) R_k = sum_g P_g,  also sum_k R_k (= P_{NG-1}).
     i128 A0 = 0, A1 = 0, SP = 0, SR = 0;
+#pragma unroll 8
     for (int k = t; k < ng; k += T) {
-        const i128 R = (i128)ntot - (i128)ng * (i128)a.rho_q[k];
+        const i128 R = (i128)ntot - (i128)ng * (i128)__ldcg(&a.rho_q[k]);
         SP += R * (i128)(ng - k);
         SR += R;
         if (k < b0) { A0 += R; A1 += R * (i128)(b0 - k); }
@@ -279,8 +238,7 @@ __global__ void __launch_bounds__(256) pic_solve_fixed_kernel(SolveArgs a) {
     const i128 sumM = (i128)ng * (A1 + Pexcl) - (i128)g * SP;
 
     NodeDiag d;
-    d.fe = 0.0;
-    for (int m = 0; m < PIC_NMODES; m++) { d.re[m] = 0.f; d.im[m] = 0.f; }
+    node_diag_reset(d);
     if (mine) {
         const double rho = a.k_rho * i128_to_f64(R);
         const double E = a.k_e * i128_to_f64(M + Mprev);
@@ -376,8 +334,7 @@ __global__ void __launch_bounds__(kSolveThreads) pic_solve_float_kernel(SolveArg
     double doff = block_exclusive_scan_f64(dsum, wt, dtot);
     const double half_dx = 0.5 * a.dx, dx2 = a.dx * a.dx;
     NodeDiag d;
-    d.fe = 0.0;
-    for (int m = 0; m < PIC_NMODES; m++) { d.re[m] = 0.f; d.im[m] = 0.f; }
+    node_diag_reset(d);
     double sprev = prev_last, charge = 0.0;
 #pragma unroll
     for (int j = 0; j < kMaxPerThread; j++) {

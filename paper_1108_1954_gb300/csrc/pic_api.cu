@@ -36,10 +36,11 @@ int validate(const pic_params *p) {
     if (!finite_pos(p->length) || !finite_pos(p->dt) || !finite_pos(p->rho_ion)) return PIC_EINVAL;
     if (!std::isfinite(p->qm) || !(p->qm < 0.0)) return PIC_EINVAL;
     if (p->sort_interval < 0 || p->history < 0) return PIC_EINVAL;
-    if (p->deposit_variant < PIC_DEPOSIT_AUTO || p->deposit_variant > PIC_DEPOSIT_MATCH_PACKED) return PIC_EINVAL;
+    if (p->deposit_variant < PIC_DEPOSIT_AUTO || p->deposit_variant > PIC_DEPOSIT_QUAD) return PIC_EINVAL;
     if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 1024 || p->block_size % 32)) return PIC_EINVAL;
+    if (p->precision == PIC_FP32_FIXED && p->block_size > 512) return PIC_EINVAL;
     if (p->blocks_per_sm < 0 || p->blocks_per_sm > 32) return PIC_EINVAL;
-    if (p->reserved != 0) return PIC_EINVAL;
+    if (p->unroll != 0 && p->unroll != 1 && p->unroll != 2 && p->unroll != 4) return PIC_EINVAL;
     return PIC_OK;
 }
 
@@ -47,7 +48,7 @@ struct Layout {
     size_t x[2], v[2];
     size_t rho_q, rho_q_last, rho_f32, rho_f64;
     size_t rho, phi, E64, E32;
-    size_t partials, dpart, hist, dev;
+    size_t partials, dpart, hist, dev, tune_rho;
     size_t s_hist, s_segtot, s_base;
     size_t total;
     int hist_len;
@@ -69,7 +70,7 @@ void sort_geometry(int64_t n, int *nchunk, long long *chunk, int *nseg, int *seg
     long long ch = (n + nc - 1) / nc;
     nc = (n + ch - 1) / ch;
     int ns = 1;
-    while ((long long)ns * ns < nc) ns++;
+    while ((long long)ns * ns < nc) ns++;   // nseg, seg_len <= 32 (nchunk <= 1024)
     *nchunk = (int)nc;
     *chunk = ch;
     *nseg = ns;
@@ -99,6 +100,7 @@ void make_layout(const pic_params *p, Layout *L) {
     L->hist_len = p->history > 0 ? p->history : kDefaultHistory;
     L->hist = take((size_t)L->hist_len * sizeof(pic_diag_row));
     L->dev = take(sizeof(DevScalars));
+    L->tune_rho = take(ng * 8);
     sort_geometry(p->npart, &L->nchunk, &L->chunk, &L->nseg, &L->seg_len);
     L->s_hist = take((size_t)L->nchunk * ng * 4);
     L->s_segtot = take((size_t)L->nseg * ng * 4);
@@ -128,7 +130,7 @@ struct pic_run {
     cudaStream_t cap = nullptr;      // private stream for graph capture
     unsigned char *ws = nullptr;
     int cur = 0;                     // which x/v buffer holds the state
-    int grid = 0, block = 0, variant = 0, solve_nb = 1;
+    int grid = 0, block = 0, variant = 0, unroll = 1, solve_nb = 1;
     int64_t step = 0;
     bool ready = false, pending_push = false;
     cudaGraphExec_t period[2] = {nullptr, nullptr};   // S steps from x parity 0/1
@@ -163,7 +165,7 @@ cudaError_t enqueue_push(pic_run *r, cudaStream_t s, bool push) {
         a.partials = r->at<double>(r->lay.partials);
         a.err = &r->dev()->err;
         a.c = r->pc;
-        return launch_push_fixed(a, r->grid, r->block, r->variant, push, s);
+        return launch_push_fixed(a, r->grid, r->block, r->variant, r->unroll, push, s);
     } else if (r->p.precision == PIC_FP32_ATOMIC) {
         PushArgsF32Atomic a;
         a.x = (float *)r->xs(c);
@@ -285,6 +287,22 @@ int capture(pic_run *r, int parity, bool sort_first, int nsteps, cudaGraphExec_t
     return cuda_fail(e);
 }
 
+// Grid of the persistent push: SMs x resident blocks, no more blocks than
+// there is work for, at most kMaxPushGrid (the partial-sum slots).
+int push_grid(const pic_run *r, int variant, int block, int unroll, int bps_cap) {
+    int bps = push_max_blocks_per_sm(r->p.precision, variant, unroll, block, r->p.ncell);
+    if (bps < 1) return 0;
+    if (bps_cap && bps_cap < bps) bps = bps_cap;
+    long long want = (long long)r->sms * bps;
+    const long long units = r->p.precision == PIC_FP32_FIXED ? (r->p.npart + 3) / 4 : r->p.npart;
+    const long long per_block = (long long)block * unroll;
+    const long long need = (units + per_block - 1) / per_block;
+    if (want > need) want = need;
+    if (want > kMaxPushGrid) want = kMaxPushGrid;
+    if (want < 1) want = 1;
+    return (int)want;
+}
+
 int check_host_positions(const pic_run *r, const void *x) {
     const int64_t n = r->p.npart;
     if (r->p.precision == PIC_FP64) {
@@ -399,19 +417,13 @@ int pic_create(const pic_params *p, void *workspace, size_t workspace_bytes,
     r->k_phi = -r->dx * r->dx * r->k_rho / (double)p->ncell;
 
     // launch shape of the fused push
-    r->variant = p->deposit_variant ? p->deposit_variant : PIC_DEPOSIT_MATCH_PACKED;
+    r->variant = p->deposit_variant ? p->deposit_variant : PIC_DEPOSIT_PACKED;
     if (p->precision != PIC_FP32_FIXED) r->variant = PIC_DEPOSIT_ATOMIC;
     r->block = p->block_size ? p->block_size : 256;
-    int bps = push_max_blocks_per_sm(p->precision, r->variant, r->block, p->ncell);
-    if (bps < 1) { delete r; return PIC_EINVAL; }
-    if (p->blocks_per_sm && p->blocks_per_sm < bps) bps = p->blocks_per_sm;
-    long long want = (long long)r->sms * bps;
-    const long long units = p->precision == PIC_FP32_FIXED ? (p->npart + 3) / 4 : p->npart;
-    const long long need = (units + r->block - 1) / r->block;
-    if (want > need) want = need;
-    if (want > kMaxPushGrid) want = kMaxPushGrid;
-    if (want < 1) want = 1;
-    r->grid = (int)want;
+    r->unroll = p->unroll ? p->unroll : 1;
+    if (p->precision != PIC_FP32_FIXED) r->unroll = 1;
+    r->grid = push_grid(r, r->variant, r->block, r->unroll, p->blocks_per_sm);
+    if (r->grid < 1) { delete r; return PIC_EINVAL; }
     r->solve_nb = solve_blocks(p->precision, p->ncell);
     *out = r;
     return PIC_OK;
@@ -572,6 +584,75 @@ int pic_launch_shape(const pic_run *run, int32_t *grid, int32_t *block, int32_t 
     if (block) *block = run->block;
     if (variant) *variant = run->variant;
     return PIC_OK;
+}
+
+int pic_autotune(pic_run *run, int32_t reps, pic_tune_entry *results,
+                 int32_t max_results, int32_t *nresults) {
+    if (!run || reps < 1) return PIC_EINVAL;
+    if (!run->ready || run->pending_push) return PIC_ESTATE;
+    if (nresults) *nresults = 0;
+    if (run->p.precision != PIC_FP32_FIXED) return PIC_OK;
+    static const int variants[] = {PIC_DEPOSIT_ATOMIC, PIC_DEPOSIT_MATCH, PIC_DEPOSIT_PACKED,
+                                   PIC_DEPOSIT_MATCH_PACKED, PIC_DEPOSIT_QUAD};
+    static const int blocks[] = {128, 256, 512};
+    static const int unrolls[] = {1, 2};
+    const size_t bytes = (size_t)run->p.npart * run->elem();
+    const int c = run->cur;
+    cudaEvent_t e0, e1;
+    PIC_CUDA(cudaEventCreate(&e0));
+    PIC_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bv = run->variant, bb = run->block, bu = run->unroll, bg = run->grid, count = 0;
+    int rc = PIC_OK;
+    for (int v : variants)
+        for (int b : blocks)
+            for (int u : unrolls) {
+                const int g = push_grid(run, v, b, u, run->p.blocks_per_sm);
+                if (g < 1) continue;
+                PushArgs a;
+                a.x = (float *)run->xs(1 - c);
+                a.v = (float *)run->vs(1 - c);
+                a.n = run->p.npart;
+                a.E32 = run->at<float>(run->lay.E32);
+                a.rho_q = run->at<unsigned long long>(run->lay.tune_rho);
+                a.partials = run->at<double>(run->lay.partials);
+                a.err = &run->dev()->err;
+                a.c = run->pc;
+                cudaError_t e = cudaMemcpyAsync(a.x, run->xs(c), bytes, cudaMemcpyDeviceToDevice, run->stream);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(a.v, run->vs(c), bytes, cudaMemcpyDeviceToDevice, run->stream);
+                if (e == cudaSuccess) e = launch_push_fixed(a, g, b, v, u, true, run->stream);  // warm
+                float times[64];
+                const int nrep = reps < 64 ? reps : 64;
+                for (int i = 0; i < nrep && e == cudaSuccess; i++) {
+                    e = cudaEventRecord(e0, run->stream);
+                    if (e == cudaSuccess) e = launch_push_fixed(a, g, b, v, u, true, run->stream);
+                    if (e == cudaSuccess) e = cudaEventRecord(e1, run->stream);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&times[i], e0, e1);
+                }
+                if (e != cudaSuccess) { rc = cuda_fail(e); goto done; }
+                // median
+                for (int i = 1; i < nrep; i++)
+                    for (int k = i; k > 0 && times[k] < times[k - 1]; k--) {
+                        float t = times[k]; times[k] = times[k - 1]; times[k - 1] = t;
+                    }
+                const float med = times[nrep / 2];
+                if (results && count < max_results) results[count] = pic_tune_entry{v, b, u, g, med};
+                count++;
+                if (med < best) { best = med; bv = v; bb = b; bu = u; bg = g; }
+            }
+    run->variant = bv;
+    run->block = bb;
+    run->unroll = bu;
+    run->grid = bg;
+    destroy_graphs(run);
+    if (nresults) *nresults = count < max_results || !results ? count : max_results;
+done:
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    PIC_CUDA(cudaMemsetAsync(run->ws + run->lay.tune_rho, 0, (size_t)run->p.ncell * 8, run->stream));
+    return read_error_word(run);
 }
 
 }  // extern "C"

@@ -10,6 +10,8 @@
 
 namespace pic {
 
+constexpr unsigned kFull = 0xffffffffu;   // all lanes of a warp
+
 // Fixed-point deposit: each particle adds exactly 2^24 to the density sum.
 constexpr int kFixBits = 24;
 constexpr uint32_t kFixOne = 1u << kFixBits;
@@ -64,10 +66,12 @@ struct PushArgsF32Atomic {
 };
 
 // Per-block share of the step diagnostics, reduced by the solve's last block.
+enum { kDiagFE = 0, kDiagKE, kDiagMom, kDiagCharge, kDiagModes,
+       kDiagFields = kDiagModes + 2 * PIC_NMODES };
 struct DiagPartial {
-    double fe, ke, mom, charge;
-    unsigned long long cq;
-    double md[2 * PIC_NMODES];     // mode sums re, im
+    double v[kDiagFields];         // field energy sum, KE and momentum sums,
+                                   // charge, mode sums (re, im) x 8
+    unsigned long long cq;         // fixed-point charge sum
 };
 
 // Field solve (fixed point: up to kSolveMaxBlocks blocks; float modes: 1).
@@ -117,14 +121,14 @@ struct SortArgs {
 
 // Launchers (each returns the launch's cudaError_t).
 cudaError_t launch_push_fixed(const PushArgs &a, int grid, int block,
-                              int variant, bool push, cudaStream_t s);
+                              int variant, int unroll, bool push, cudaStream_t s);
 cudaError_t launch_push_f32_atomic(const PushArgsF32Atomic &a, int grid,
                                    int block, bool push, cudaStream_t s);
 cudaError_t launch_push_f64(const PushArgs64 &a, int grid, int block,
                             bool push, cudaStream_t s);
 size_t push_smem_bytes(int mode, int ng);
 cudaError_t push_prepare_attributes(int mode, int ng);
-int push_max_blocks_per_sm(int mode, int variant, int block, int ng);
+int push_max_blocks_per_sm(int mode, int variant, int unroll, int block, int ng);
 
 cudaError_t launch_solve(const SolveArgs &a, cudaStream_t s);
 constexpr int kSolveThreads = 1024;

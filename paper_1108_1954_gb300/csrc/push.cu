@@ -20,15 +20,17 @@
 //                 by __reduce_add_sync and its first lane does two atomics;
 //   PACKED        one atomic per particle on a packed (count << 40 | sum W)
 //                 word per left node, unpacked when the tile is flushed;
-//   MATCH_PACKED  the two combined: one atomic per warp group.
+//   MATCH_PACKED  the two combined: one atomic per warp group;
+//   QUAD          runs of equal left node among a thread's 4 particles are
+//                 summed in registers, then two atomics per run.
 // The packed forms flush the tile to global memory before any node can hold
 // 2^16 particles, so the 40-bit weight field never carries into the count.
-#include "pic_internal.cuh"
+// The unpacked tiles hold exact 64-bit sums in two 32-bit words (below).
+#include "particle_ops.cuh"
 
 namespace pic {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMatchPacked = PIC_DEPOSIT_MATCH_PACKED;
 constexpr unsigned long long kPackShift = 40;
 constexpr unsigned long long kPackMask = (1ull << kPackShift) - 1ull;
@@ -37,100 +39,120 @@ constexpr int kPackLimit = 65535 - 32;
 
 using u64 = unsigned long long;
 
-// Left/right node and fraction of a float32 position, by the fixed-point
-// recipe: s = x*c - 1/2, i = floor(s), f = s - i, each one float operation
-// rounded to nearest (no contraction).  ok is false for a position that is not
-// finite or lies outside the grid.
-struct NodePair {
-    int il, ir;
-    float f;
-    bool ok;
+// Shared-memory density tiles.  GB300 has no single-instruction 64-bit
+// integer add on shared memory (it runs as a compare-and-swap loop, which
+// serialises badly when the lanes of a warp hit one node), so the unpacked
+// variants keep each node's 64-bit sum as two 32-bit words: a 32-bit
+// fetch-add on the low word, and +1 on the high word from the one add that
+// wraps it.  The packed variants keep one 64-bit word per left node
+// (count << 40 | sum W) and use the 64-bit add.
+// Both tiles are ghost-padded: index j is node (j-1) mod NG, j = 0..NG+1.
+struct Tile {
+    unsigned *lo, *hi;      // unpacked: 32-bit halves of the node sums
+    u64 *packed;            // packed: one word per left node
 };
 
-__device__ __forceinline__ NodePair locate(float x, const PushConsts &c) {
-    NodePair p;
-    const float u = __fmul_rn(x, c.inv_dx);
-    const float s = __fsub_rn(u, 0.5f);
-    const float fl = floorf(s);
-    p.f = __fsub_rn(s, fl);
-    p.ok = (fl >= -1.0f) && (fl <= (float)(c.ng - 1));
-    const int i = p.ok ? (int)fl : 0;
-    p.il = (i < 0) ? i + c.ng : i;
-    p.ir = (i + 1 >= c.ng) ? i + 1 - c.ng : i + 1;
-    return p;
+__device__ __forceinline__ void tile_add(const Tile &t, unsigned j, unsigned val) {
+    const unsigned old = atomicAdd(&t.lo[j], val);
+    if (old + val < old) atomicAdd(&t.hi[j], 1u);
 }
 
-// The right node's share W = trunc(f * 2^24) of a particle's 2^24.
-__device__ __forceinline__ unsigned fixed_weight(float f) {
-    return __float2uint_rz(__fmul_rn(f, 16777216.0f));
-}
-
-// Gather E at x (linear weights of the two nearest nodes), kick, drift, wrap.
-__device__ __forceinline__ void push_particle(float &x, float &v, const float *sE,
-                                              const PushConsts &c, float &ke,
-                                              float &mom) {
-    const NodePair p = locate(x, c);
-    const float e0 = sE[p.il], e1 = sE[p.ir];
-    const float ep = p.ok ? fmaf(p.f, e1 - e0, e0) : 0.0f;
-    const float vn = fmaf(c.qmdt, ep, v);
-    ke = fmaf(v, vn, ke);
-    mom += vn;
-    float xn = fmaf(vn, c.dt, x);
-    if (xn < 0.0f) xn += c.length;
-    else if (xn >= c.length) xn -= c.length;
-    if (xn >= c.length) xn = 0.0f;  // x + L rounded up to L: the point 0
-    x = xn;
-    v = vn;
-}
-
-// Deposit one particle (valid lanes only; all 32 lanes of the warp call this
-// together for the MATCH variants).
+// Deposit one particle (all 32 lanes of the warp call this together for the
+// MATCH variants).
 template <int VARIANT>
-__device__ __forceinline__ void deposit(u64 *sRho, float x, bool valid,
-                                        const PushConsts &c, unsigned *err,
-                                        int lane) {
-    const NodePair p = locate(x, c);
-    const bool good = valid && p.ok;
-    if (valid && !p.ok) atomicOr(err, kErrPosition);
-    const unsigned W = good ? fixed_weight(p.f) : 0u;
-    if (VARIANT == PIC_DEPOSIT_ATOMIC) {
-        if (good) {
-            atomicAdd(&sRho[p.il], (u64)(kFixOne - W));
-            atomicAdd(&sRho[p.ir], (u64)W);
+__device__ __forceinline__ void deposit_one(const Tile &t, float x, bool valid,
+                                            const PushConsts &c, unsigned *err, int lane) {
+    const Loc l = locate(x, c.inv_dx);
+    const bool ok = valid && l.j <= (unsigned)c.ng;
+    if (valid && !ok) atomicOr(err, kErrPosition);
+    const unsigned W = ok ? fixed_weight(l.f) : 0u;
+    if (VARIANT == PIC_DEPOSIT_ATOMIC || VARIANT == PIC_DEPOSIT_QUAD) {
+        if (ok) {
+            tile_add(t, l.j, kFixOne - W);
+            tile_add(t, l.j + 1, W);
         }
     } else if (VARIANT == PIC_DEPOSIT_PACKED) {
-        if (good) atomicAdd(&sRho[p.il], (1ull << kPackShift) | (u64)W);
+        if (ok) atomicAdd(&t.packed[l.j], (1ull << kPackShift) | (u64)W);
     } else {
-        const unsigned key = good ? (unsigned)p.il : 0xffffffffu;
+        const unsigned key = ok ? l.j : 0xffffffffu;
         const unsigned peers = __match_any_sync(kFull, key);
         const unsigned wsum = __reduce_add_sync(peers, W);
-        if (good && lane == __ffs(peers) - 1) {
-            const u64 cnt = (u64)__popc(peers);
+        if (ok && lane == __ffs(peers) - 1) {
+            const unsigned cnt = (unsigned)__popc(peers);
             if (VARIANT == PIC_DEPOSIT_MATCH) {
-                atomicAdd(&sRho[p.il], cnt * kFixOne - (u64)wsum);
-                atomicAdd(&sRho[p.ir], (u64)wsum);
+                // cnt * 2^24 - wsum <= 2^29: fits the 32-bit add
+                tile_add(t, l.j, (cnt << kFixBits) - wsum);
+                tile_add(t, l.j + 1, wsum);
             } else {
-                atomicAdd(&sRho[p.il], (cnt << kPackShift) + (u64)wsum);
+                atomicAdd(&t.packed[l.j], ((u64)cnt << kPackShift) + (u64)wsum);
             }
         }
     }
 }
 
-// Add the block's tile to the global density and clear it.
+// Deposit the 4 particles of a float4 group (valid per lane).
+template <int VARIANT>
+__device__ __forceinline__ void deposit4(const Tile &t, const float4 &xx, bool valid,
+                                         const PushConsts &c, unsigned *err, int lane) {
+    const float xs[4] = {xx.x, xx.y, xx.z, xx.w};
+    if (VARIANT == PIC_DEPOSIT_QUAD) {
+        // consecutive particles of the group with equal left node are summed
+        // in registers first (at most 4 * 2^24 per word), then added once
+        unsigned key = 0xffffffffu, left = 0, right = 0;
+        bool bad = false;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const Loc l = locate(xs[k], c.inv_dx);
+            const bool ok = valid && l.j <= (unsigned)c.ng;
+            bad |= valid && !ok;
+            const unsigned W = fixed_weight(l.f);
+            if (ok && l.j == key) {
+                left += kFixOne - W;
+                right += W;
+            } else if (ok) {
+                if (key != 0xffffffffu) {
+                    tile_add(t, key, left);
+                    tile_add(t, key + 1, right);
+                }
+                key = l.j;
+                left = kFixOne - W;
+                right = W;
+            }
+        }
+        if (key != 0xffffffffu) {
+            tile_add(t, key, left);
+            tile_add(t, key + 1, right);
+        }
+        if (bad) atomicOr(err, kErrPosition);
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) deposit_one<VARIANT>(t, xs[k], valid, c, err, lane);
+}
+
+// Add the block's tile to the global density and clear it (ghost nodes
+// folded onto their periodic images).
 template <bool PACKED>
-__device__ __forceinline__ void flush_tile(u64 *sRho, u64 *rho_q, int ng) {
+__device__ __forceinline__ void flush_tile(const Tile &t, u64 *rho_q, int ng) {
     __syncthreads();
-    for (int g = threadIdx.x; g < ng; g += blockDim.x) {
-        const u64 t = sRho[g];
-        if (t == 0) continue;
-        sRho[g] = 0;
+    const int top = PACKED ? ng : ng + 1;     // last used tile index
+    for (int j = threadIdx.x; j <= top; j += blockDim.x) {
+        const int left = j == 0 ? ng - 1 : j - 1;      // node of index j
         if (PACKED) {
-            const u64 cnt = t >> kPackShift, sw = t & kPackMask;
-            const u64 left = cnt * kFixOne - sw;
-            if (left) atomicAdd(&rho_q[g], left);
-            if (sw) atomicAdd(&rho_q[g + 1 == ng ? 0 : g + 1], sw);
+            const u64 w = t.packed[j];
+            if (w == 0) continue;
+            t.packed[j] = 0;
+            const u64 cnt = w >> kPackShift, sw = w & kPackMask;
+            const u64 lw = cnt * kFixOne - sw;
+            const int right = j == ng ? 0 : j;
+            if (lw) atomicAdd(&rho_q[left], lw);
+            if (sw) atomicAdd(&rho_q[right], sw);
         } else {
-            atomicAdd(&rho_q[g], t);
+            const u64 w = ((u64)t.hi[j] << 32) | (u64)t.lo[j];
+            if (w == 0) continue;
+            t.lo[j] = 0u;
+            t.hi[j] = 0u;
+            atomicAdd(&rho_q[j == ng + 1 ? 0 : left], w);
         }
     }
     __syncthreads();
@@ -156,18 +178,25 @@ __device__ __forceinline__ void block_sum2(double &a, double &b, double *scratch
     }
 }
 
-template <int VARIANT, bool PUSH>
-__global__ void __launch_bounds__(1024) pic_push_fixed_kernel(PushArgs a) {
+// One block-iteration covers U*blockDim consecutive float4 groups; thread t
+// takes groups q0 + u*blockDim + t (coalesced for each u).  The next
+// iteration's groups are loaded before the current ones are processed.
+template <int VARIANT, bool PUSH, int U>
+__global__ void __launch_bounds__(512) pic_push_fixed_kernel(PushArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[64];
     constexpr bool kPacked = VARIANT == PIC_DEPOSIT_PACKED || VARIANT == kMatchPacked;
     const PushConsts c = a.c;
-    u64 *sRho = reinterpret_cast<u64 *>(smem_raw);
-    float *sE = reinterpret_cast<float *>(sRho + c.ng);
+    const int ng = c.ng;
+    Tile tile;                                                       // 8 (ng + 2) B
+    tile.packed = reinterpret_cast<u64 *>(smem_raw);
+    tile.lo = reinterpret_cast<unsigned *>(smem_raw);
+    tile.hi = tile.lo + ng + 2;
+    float *sE = reinterpret_cast<float *>(smem_raw + 8 * (ng + 2));  // ng + 2
     const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31;
-    for (int g = tid; g < c.ng; g += bs) {
-        sRho[g] = 0;
-        if (PUSH) sE[g] = a.E32[g];
+    for (int j = tid; j < ng + 2; j += bs) {
+        tile.packed[j] = 0;
+        if (PUSH) sE[j] = a.E32[j == 0 ? ng - 1 : (j == ng + 1 ? 0 : j - 1)];
     }
     __syncthreads();
 
@@ -175,37 +204,53 @@ __global__ void __launch_bounds__(1024) pic_push_fixed_kernel(PushArgs a) {
     const long long n4 = a.n >> 2;
     float4 *x4 = reinterpret_cast<float4 *>(a.x);
     float4 *v4 = reinterpret_cast<float4 *>(a.v);
-    const long long stride = (long long)gridDim.x * bs;
-    const int flush_every = kPacked ? max(1, kPackLimit / (4 * bs)) : 0;
+    const long long span = (long long)bs * U;
+    const long long stride = (long long)gridDim.x * span;
+    const int flush_every = kPacked ? max(1, kPackLimit / (int)(4 * span)) : 0;
     int since_flush = 0;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 cx[U], cv[U];
+    long long q0 = (long long)blockIdx.x * span;
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const long long q = q0 + u * bs + tid;
+        cx[u] = q < n4 ? __ldcs(x4 + q) : zero4;
+        cv[u] = (PUSH && q < n4) ? __ldcs(v4 + q) : zero4;
+    }
     // The trip count is uniform over the block (q0 is), so the packed flush
     // may synchronise inside the loop and every warp is converged for match.
-    for (long long q0 = (long long)blockIdx.x * bs; q0 < n4; q0 += stride) {
-        const long long q = q0 + tid;
-        const bool valid = q < n4;
-        float4 xx = make_float4(0.f, 0.f, 0.f, 0.f), vv = xx;
-        if (valid) {
-            xx = __ldcs(x4 + q);
-            if (PUSH) vv = __ldcs(v4 + q);
+    for (; q0 < n4; q0 += stride) {
+        float4 nx[U], nv[U];
+        const long long q1 = q0 + stride;
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const long long q = q1 + u * bs + tid;
+            nx[u] = q < n4 ? __ldcs(x4 + q) : zero4;
+            nv[u] = (PUSH && q < n4) ? __ldcs(v4 + q) : zero4;
         }
-        if (PUSH && valid) {
-            push_particle(xx.x, vv.x, sE, c, ke, mom);
-            push_particle(xx.y, vv.y, sE, c, ke, mom);
-            push_particle(xx.z, vv.z, sE, c, ke, mom);
-            push_particle(xx.w, vv.w, sE, c, ke, mom);
-        }
-        deposit<VARIANT>(sRho, xx.x, valid, c, a.err, lane);
-        deposit<VARIANT>(sRho, xx.y, valid, c, a.err, lane);
-        deposit<VARIANT>(sRho, xx.z, valid, c, a.err, lane);
-        deposit<VARIANT>(sRho, xx.w, valid, c, a.err, lane);
-        if (PUSH && valid) {
-            __stcs(x4 + q, xx);
-            __stcs(v4 + q, vv);
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const long long q = q0 + u * bs + tid;
+            const bool valid = q < n4;
+            float4 xx = cx[u], vv = cv[u];
+            if (PUSH && valid) {
+                push_particle(xx.x, vv.x, sE, c, ke, mom);
+                push_particle(xx.y, vv.y, sE, c, ke, mom);
+                push_particle(xx.z, vv.z, sE, c, ke, mom);
+                push_particle(xx.w, vv.w, sE, c, ke, mom);
+            }
+            deposit4<VARIANT>(tile, xx, valid, c, a.err, lane);
+            if (PUSH && valid) {
+                __stcs(x4 + q, xx);
+                __stcs(v4 + q, vv);
+            }
         }
         if (kPacked && ++since_flush == flush_every) {
-            flush_tile<true>(sRho, a.rho_q, c.ng);
+            flush_tile<true>(tile, a.rho_q, ng);
             since_flush = 0;
         }
+#pragma unroll
+        for (int u = 0; u < U; u++) { cx[u] = nx[u]; cv[u] = nv[u]; }
     }
     // The last N mod 4 particles: warp 0 of block 0, converged.
     if (blockIdx.x == 0 && tid < 32) {
@@ -213,7 +258,7 @@ __global__ void __launch_bounds__(1024) pic_push_fixed_kernel(PushArgs a) {
         const bool valid = i < a.n;
         float xs = valid ? a.x[i] : 0.0f, vs = valid && PUSH ? a.v[i] : 0.0f;
         if (PUSH && valid) push_particle(xs, vs, sE, c, ke, mom);
-        deposit<VARIANT>(sRho, xs, valid, c, a.err, lane);
+        deposit_one<VARIANT>(tile, xs, valid, c, a.err, lane);
         if (PUSH && valid) { a.x[i] = xs; a.v[i] = vs; }
     }
     if (PUSH) {
@@ -225,7 +270,7 @@ __global__ void __launch_bounds__(1024) pic_push_fixed_kernel(PushArgs a) {
             a.partials[2 * blockIdx.x + 1] = dmom;
         }
     }
-    flush_tile<kPacked>(sRho, a.rho_q, c.ng);
+    flush_tile<kPacked>(tile, a.rho_q, ng);
 }
 
 // ---- float32 push with float32 atomic deposit (precision study) -------------
@@ -235,12 +280,13 @@ __global__ void __launch_bounds__(1024) pic_push_f32atomic_kernel(PushArgsF32Ato
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[64];
     const PushConsts c = a.c;
-    float *sRho = reinterpret_cast<float *>(smem_raw);
-    float *sE = sRho + c.ng;
+    const int ng = c.ng;
+    float *sRho = reinterpret_cast<float *>(smem_raw);   // ng + 2, ghost-padded
+    float *sE = sRho + ng + 2;                            // ng + 2, ghost-padded
     const int tid = threadIdx.x, bs = blockDim.x;
-    for (int g = tid; g < c.ng; g += bs) {
-        sRho[g] = 0.0f;
-        if (PUSH) sE[g] = a.E32[g];
+    for (int j = tid; j < ng + 2; j += bs) {
+        sRho[j] = 0.0f;
+        if (PUSH) sE[j] = a.E32[j == 0 ? ng - 1 : (j == ng + 1 ? 0 : j - 1)];
     }
     __syncthreads();
     float ke = 0.0f, mom = 0.0f;
@@ -248,10 +294,10 @@ __global__ void __launch_bounds__(1024) pic_push_f32atomic_kernel(PushArgsF32Ato
     for (long long i = (long long)blockIdx.x * bs + tid; i < a.n; i += stride) {
         float x = a.x[i], v = PUSH ? a.v[i] : 0.0f;
         if (PUSH) push_particle(x, v, sE, c, ke, mom);
-        const NodePair p = locate(x, c);
-        if (p.ok) {
-            atomicAdd(&sRho[p.il], 1.0f - p.f);
-            atomicAdd(&sRho[p.ir], p.f);
+        const Loc l = locate(x, c.inv_dx);
+        if (l.j <= (unsigned)ng) {
+            atomicAdd(&sRho[l.j], 1.0f - l.f);
+            atomicAdd(&sRho[l.j + 1], l.f);
         } else {
             atomicOr(a.err, kErrPosition);
         }
@@ -267,8 +313,12 @@ __global__ void __launch_bounds__(1024) pic_push_f32atomic_kernel(PushArgsF32Ato
         }
     }
     __syncthreads();
-    for (int g = tid; g < c.ng; g += bs)
-        if (sRho[g] != 0.0f) atomicAdd(&a.rho_acc[g], sRho[g]);
+    for (int j = tid; j < ng + 2; j += bs) {
+        const float t = sRho[j];
+        if (t == 0.0f) continue;
+        const int node = j == 0 ? ng - 1 : (j == ng + 1 ? 0 : j - 1);
+        atomicAdd(&a.rho_acc[node], t);
+    }
 }
 
 // ---- float64 push with float64 atomic deposit (precision study) ------------
@@ -336,22 +386,25 @@ __global__ void __launch_bounds__(1024) pic_push_f64_kernel(PushArgs64 a) {
 
 using FixedKernel = void (*)(PushArgs);
 
-FixedKernel pick_fixed(int variant, bool push) {
+template <int V>
+FixedKernel pick_unroll(bool push, int unroll) {
+    if (!push) return &pic_push_fixed_kernel<V, false, 1>;
+    switch (unroll) {
+        case 1: return &pic_push_fixed_kernel<V, true, 1>;
+        case 2: return &pic_push_fixed_kernel<V, true, 2>;
+        case 4: return &pic_push_fixed_kernel<V, true, 4>;
+        default: return nullptr;
+    }
+}
+
+FixedKernel pick_fixed(int variant, bool push, int unroll) {
     switch (variant) {
-        case PIC_DEPOSIT_ATOMIC:
-            return push ? &pic_push_fixed_kernel<PIC_DEPOSIT_ATOMIC, true>
-                        : &pic_push_fixed_kernel<PIC_DEPOSIT_ATOMIC, false>;
-        case PIC_DEPOSIT_MATCH:
-            return push ? &pic_push_fixed_kernel<PIC_DEPOSIT_MATCH, true>
-                        : &pic_push_fixed_kernel<PIC_DEPOSIT_MATCH, false>;
-        case PIC_DEPOSIT_PACKED:
-            return push ? &pic_push_fixed_kernel<PIC_DEPOSIT_PACKED, true>
-                        : &pic_push_fixed_kernel<PIC_DEPOSIT_PACKED, false>;
-        case kMatchPacked:
-            return push ? &pic_push_fixed_kernel<kMatchPacked, true>
-                        : &pic_push_fixed_kernel<kMatchPacked, false>;
-        default:
-            return nullptr;
+        case PIC_DEPOSIT_ATOMIC: return pick_unroll<PIC_DEPOSIT_ATOMIC>(push, unroll);
+        case PIC_DEPOSIT_MATCH: return pick_unroll<PIC_DEPOSIT_MATCH>(push, unroll);
+        case PIC_DEPOSIT_PACKED: return pick_unroll<PIC_DEPOSIT_PACKED>(push, unroll);
+        case kMatchPacked: return pick_unroll<kMatchPacked>(push, unroll);
+        case PIC_DEPOSIT_QUAD: return pick_unroll<PIC_DEPOSIT_QUAD>(push, unroll);
+        default: return nullptr;
     }
 }
 
@@ -359,8 +412,8 @@ FixedKernel pick_fixed(int variant, bool push) {
 
 size_t push_smem_bytes(int mode, int ng) {
     if (mode == PIC_FP64) return (size_t)ng * 16;
-    if (mode == PIC_FP32_ATOMIC) return (size_t)ng * 8;
-    return (size_t)ng * 12;
+    if (mode == PIC_FP32_ATOMIC) return (size_t)(ng + 2) * 8;
+    return (size_t)(ng + 2) * 12;
 }
 
 cudaError_t push_prepare_attributes(int mode, int ng) {
@@ -368,12 +421,14 @@ cudaError_t push_prepare_attributes(int mode, int ng) {
     (void)ng;
     cudaError_t e = cudaSuccess;
     if (mode == PIC_FP32_FIXED) {
-        for (int v = PIC_DEPOSIT_ATOMIC; v <= kMatchPacked; v++)
-            for (int p = 0; p < 2; p++) {
-                e = cudaFuncSetAttribute(pick_fixed(v, p != 0),
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-                if (e != cudaSuccess) return e;
-            }
+        const int unrolls[3] = {1, 2, 4};
+        for (int v = PIC_DEPOSIT_ATOMIC; v <= PIC_DEPOSIT_QUAD; v++)
+            for (int p = 0; p < 2; p++)
+                for (int u : unrolls) {
+                    e = cudaFuncSetAttribute(pick_fixed(v, p != 0, u),
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+                    if (e != cudaSuccess) return e;
+                }
     } else if (mode == PIC_FP32_ATOMIC) {
         e = cudaFuncSetAttribute(&pic_push_f32atomic_kernel<true>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -390,12 +445,12 @@ cudaError_t push_prepare_attributes(int mode, int ng) {
     return e;
 }
 
-int push_max_blocks_per_sm(int mode, int variant, int block, int ng) {
+int push_max_blocks_per_sm(int mode, int variant, int unroll, int block, int ng) {
     int nb = 0;
     const size_t smem = push_smem_bytes(mode, ng);
     cudaError_t e;
     if (mode == PIC_FP32_FIXED)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pick_fixed(variant, true), block, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pick_fixed(variant, true, unroll), block, smem);
     else if (mode == PIC_FP32_ATOMIC)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, &pic_push_f32atomic_kernel<true>, block, smem);
     else
@@ -404,8 +459,8 @@ int push_max_blocks_per_sm(int mode, int variant, int block, int ng) {
 }
 
 cudaError_t launch_push_fixed(const PushArgs &a, int grid, int block, int variant,
-                              bool push, cudaStream_t s) {
-    FixedKernel k = pick_fixed(variant, push);
+                              int unroll, bool push, cudaStream_t s) {
+    FixedKernel k = pick_fixed(variant, push, unroll);
     if (!k) return cudaErrorInvalidValue;
     k<<<grid, block, push_smem_bytes(PIC_FP32_FIXED, a.c.ng), s>>>(a);
     return cudaGetLastError();

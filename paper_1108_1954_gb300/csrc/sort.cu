@@ -22,8 +22,8 @@
 namespace pic {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
 constexpr unsigned kNoKey = 0xffffffffu;
+constexpr int kMaxSegLen = 32;   // chunks per segment and segments (<= 32 each)
 
 template <typename T>
 __device__ __forceinline__ unsigned cell_key(T x, T inv_dx, int ng) {
@@ -43,12 +43,22 @@ __global__ void __launch_bounds__(kSortThreads) sort_count_kernel(SortArgs<T> a)
     const long long start = (long long)blockIdx.x * a.chunk;
     const long long end = min(a.n, start + a.chunk);
     const int lane = threadIdx.x & 31;
-    for (long long i0 = start; i0 < end; i0 += blockDim.x) {
-        const long long i = i0 + threadIdx.x;
-        const bool valid = i < end;
-        const unsigned key = valid ? cell_key(a.x[i], a.inv_dx, ng) : kNoKey;
-        const unsigned peers = __match_any_sync(kFull, key);
-        if (valid && lane == __ffs(peers) - 1) atomicAdd(&sh_count[key], (unsigned)__popc(peers));
+    constexpr int K = 4;
+    for (long long i0 = start; i0 < end; i0 += K * blockDim.x) {
+        T xv[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const long long i = i0 + k * blockDim.x + threadIdx.x;
+            xv[k] = i < end ? __ldcs(a.x + i) : (T)0;
+        }
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const long long i = i0 + k * blockDim.x + threadIdx.x;
+            const bool valid = i < end;
+            const unsigned key = valid ? cell_key(xv[k], a.inv_dx, ng) : kNoKey;
+            const unsigned peers = __match_any_sync(kFull, key);
+            if (valid && lane == __ffs(peers) - 1) atomicAdd(&sh_count[key], (unsigned)__popc(peers));
+        }
     }
     __syncthreads();
     unsigned *row = a.hist + (size_t)blockIdx.x * ng;
@@ -61,18 +71,21 @@ __global__ void __launch_bounds__(256) sort_colscan_kernel(SortArgs<T> a) {
     if (g >= a.ng) return;
     const int seg = blockIdx.y;
     const int b0 = seg * a.seg_len, b1 = min(a.nchunk, b0 + a.seg_len);
+    unsigned c[kMaxSegLen];
+#pragma unroll
+    for (int k = 0; k < kMaxSegLen; k++)
+        c[k] = b0 + k < b1 ? a.hist[(size_t)(b0 + k) * a.ng + g] : 0u;
     unsigned run = 0;
-    for (int b = b0; b < b1; b++) {
-        unsigned *p = a.hist + (size_t)b * a.ng + g;
-        const unsigned c = *p;
-        *p = run;
-        run += c;
+#pragma unroll
+    for (int k = 0; k < kMaxSegLen; k++) {
+        if (b0 + k < b1) a.hist[(size_t)(b0 + k) * a.ng + g] = run;
+        run += c[k];
     }
     a.segtot[(size_t)seg * a.ng + g] = run;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(1024) sort_base_kernel(SortArgs<T> a) {
+__global__ void __launch_bounds__(512) sort_base_kernel(SortArgs<T> a) {
     __shared__ unsigned wt[32];
     const int ng = a.ng, T_ = blockDim.x, t = threadIdx.x;
     const int k = (ng + T_ - 1) / T_;
@@ -81,12 +94,14 @@ __global__ void __launch_bounds__(1024) sort_base_kernel(SortArgs<T> a) {
     for (int j = 0; j < k; j++) {
         const int g = g0 + j;
         if (g >= ng) break;
+        unsigned c[kMaxSegLen];
+#pragma unroll
+        for (int s = 0; s < kMaxSegLen; s++) c[s] = s < a.nseg ? a.segtot[(size_t)s * ng + g] : 0u;
         unsigned run = 0;
-        for (int s = 0; s < a.nseg; s++) {
-            unsigned *p = a.segtot + (size_t)s * ng + g;
-            const unsigned c = *p;
-            *p = run;
-            run += c;
+#pragma unroll
+        for (int s = 0; s < kMaxSegLen; s++) {
+            if (s < a.nseg) a.segtot[(size_t)s * ng + g] = run;
+            run += c[s];
         }
         a.base[g] = run;   // cell total for now
         local += run;
@@ -125,11 +140,15 @@ __global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(SortArgs<T> 
     const long long end = min(a.n, start + a.chunk);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
+    T nx = start + threadIdx.x < end ? __ldcs(a.x + start + threadIdx.x) : (T)0;
+    T nv = start + threadIdx.x < end ? __ldcs(a.v + start + threadIdx.x) : (T)0;
     for (long long i0 = start; i0 < end; i0 += blockDim.x) {
         const long long i = i0 + threadIdx.x;
         const bool valid = i < end;
-        const T x = valid ? a.x[i] : (T)0;
-        const T v = valid ? a.v[i] : (T)0;
+        const T x = nx, v = nv;
+        const long long inext = i + blockDim.x;
+        nx = inext < end ? __ldcs(a.x + inext) : (T)0;
+        nv = inext < end ? __ldcs(a.v + inext) : (T)0;
         const unsigned key = valid ? cell_key(x, a.inv_dx, ng) : kNoKey;
         const unsigned peers = __match_any_sync(kFull, key);
         const int leader = __ffs(peers) - 1;
@@ -163,7 +182,7 @@ cudaError_t launch_sort_t(const SortArgs<T> &a, cudaStream_t s) {
     dim3 cg((a.ng + 255) / 256, a.nseg);
     sort_colscan_kernel<T><<<cg, 256, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    sort_base_kernel<T><<<1, 1024, 0, s>>>(a);
+    sort_base_kernel<T><<<1, 512, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     sort_scatter_kernel<T><<<a.nchunk, kSortThreads, smem, s>>>(a);
     return cudaGetLastError();

@@ -99,16 +99,17 @@ def test_one_step_parity(n, ng):
     one_step_parity(n, ng, L4PI, seed=n + ng)
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
-@pytest.mark.parametrize("block", [64, 256, 1024])
-def test_deposit_variants_and_shapes_identical(variant, block):
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("block", [64, 256, 512])
+@pytest.mark.parametrize("unroll", [1, 2, 4])
+def test_deposit_variants_and_shapes_identical(variant, block, unroll):
     n, ng = 70001, 512
     x, v = W.two_stream(n, L4PI, 0.2, 0.01, 3)
     x32, v32 = W.to_f32_state(x, v, L4PI)
     ref = make_run(n, ng, L4PI, deposit_variant=1, block_size=256)
     ref.init(x32, v32)
     ref.step_n(3)
-    run = make_run(n, ng, L4PI, deposit_variant=variant, block_size=block)
+    run = make_run(n, ng, L4PI, deposit_variant=variant, block_size=block, unroll=unroll)
     run.init(x32, v32)
     run.step_n(3)
     assert np.array_equal(run.get_field()["rho_q"], ref.get_field()["rho_q"])
@@ -123,7 +124,7 @@ def test_packed_flush_with_all_particles_in_one_cell():
     n, ng, L = 300001, 64, 64.0
     x32 = np.full(n, 10.3, dtype=np.float32)
     v32 = np.zeros(n, dtype=np.float32)
-    for variant in (3, 4):
+    for variant in (3, 4, 5):
         run = make_run(n, ng, L, deposit_variant=variant, block_size=256, blocks_per_sm=1)
         run.init(x32, v32)
         assert np.array_equal(run.get_field()["rho_q"], O.deposit_fixed(ng, L, x32))
@@ -220,3 +221,29 @@ def test_deposit_then_solve_reproduces_the_field():
     g = run.get_field()
     assert run.step == 5
     assert np.array_equal(f["rho_q"], g["rho_q"]) and np.array_equal(f["E"], g["E"])
+
+
+def test_autotune_leaves_state_and_results_unchanged():
+    n, ng = 300001, 1024
+    x, v = W.two_stream(n, L4PI, 0.2, 0.01, 12)
+    x32, v32 = W.to_f32_state(x, v, L4PI)
+    a = make_run(n, ng, L4PI, sort_interval=5)
+    b = make_run(n, ng, L4PI, sort_interval=5)
+    a.init(x32, v32)
+    b.init(x32, v32)
+    a.step_n(7)
+    b.step_n(7)
+    table = a.autotune(reps=2)
+    assert len(table) >= 20 and (table["ms"] > 0).all()
+    g, blk, var = a.launch_shape()
+    best = table[np.argmin(table["ms"])]
+    assert (var, blk) == (int(best["variant"]), int(best["block"]))
+    xa, va = a.get_state()
+    xb, vb = b.get_state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    a.step_n(9)
+    b.step_n(9)
+    xa, va = a.get_state()
+    xb, vb = b.get_state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    assert np.array_equal(a.get_field()["rho_q"], b.get_field()["rho_q"])
