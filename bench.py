@@ -47,7 +47,7 @@ REF_SAMPLE = 1 << 20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=["c2", "small"])
@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--bps", type=int, default=0)
     ap.add_argument("--unroll", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-runs", type=int, default=512)
+    ap.add_argument("--batched-steps", type=int, default=500)
     return ap.parse_args()
 
 
@@ -94,7 +97,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -245,6 +248,104 @@ def time_e2e(args, w, x32, v32):
     return dict(value=n * K / el, seconds=el, h2d_per_step=h2d / K, d2h_per_step=d2h / K)
 
 
+def ensemble_states(nrun, seed):
+    """The batched ensemble: per run (params, x32, v32)."""
+    import workloads as W
+    import paper_1108_1954_gb300 as pic
+    out = []
+    for r in W.ensemble_runs(nrun, seed):
+        x, v = W.two_stream(r["npart"], r["length"], r["v0"], r["vth"], r["seed"],
+                            modes=((1, 1e-3, 0.0),))
+        x32, v32 = W.to_f32_state(x, v, r["length"])
+        out.append((pic.Params(npart=r["npart"], ncell=r["ncell"], length=r["length"],
+                               dt=r["dt"]), x32, v32))
+    return out
+
+
+def tune_pool(states, steps, history):
+    """Autotuner of the batched launch: time each (variant, cluster, block) on
+    a size-stratified sample of the runs; returns the fastest and the table."""
+    import torch
+    import paper_1108_1954_gb300 as pic
+    order = sorted(range(len(states)), key=lambda i: states[i][0].npart)
+    sample = [states[i] for i in order[:: max(1, len(order) // 48)]]
+    nbytes = sum(pic.pool_run_bytes(p, history) for p, _, _ in sample) + (64 << 20)
+    table = []
+    for variant in (1, 2, 5):
+        for cluster in (2, 4, 8):
+            for block in (256, 512):
+                try:
+                    pool = pic.Pool(max_slots=len(sample), ncell_max=2048, arena_bytes=nbytes,
+                                    history=history, variant=variant, cluster=cluster,
+                                    block=block)
+                except pic.PicError:
+                    continue
+                for p, x, v in sample:
+                    pool.admit(p, x, v, steps)
+                pool.advance(0)
+                pool.sync()
+                e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+                e0.record(pool.stream)
+                pool.advance(steps)
+                e1.record(pool.stream)
+                pool.sync()
+                table.append(((variant, cluster, block), e0.elapsed_time(e1)))
+                pool.close()
+                del pool
+    table.sort(key=lambda t: t[1])
+    return table[0][0], table
+
+
+def time_batched(args):
+    """Config 3: the ensemble in one persistent cluster launch vs the same
+    runs one per launch (each through pic_step_n, CUDA graphs)."""
+    import torch
+    import paper_1108_1954_gb300 as pic
+    K, H = args.batched_steps, 16
+    states = ensemble_states(args.batched_runs, 3)
+    total_particles = sum(p.npart for p, _, _ in states)
+    best, table = tune_pool(states, 20, H)
+    nbytes = sum(pic.pool_run_bytes(p, H) for p, _, _ in states) + (64 << 20)
+    pool = pic.Pool(max_slots=len(states), ncell_max=2048, arena_bytes=nbytes, history=H,
+                    variant=best[0], cluster=best[1], block=best[2])
+    for p, x, v in states:
+        pool.admit(p, x, v, K)
+    pool.advance(0)
+    pool.sync()
+    e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+    e0.record(pool.stream)
+    pool.advance(K)
+    e1.record(pool.stream)
+    pool.sync()
+    t_batched = e0.elapsed_time(e1) / 1e3
+    pool.close()
+    del pool
+    # one run per launch sequence: every run through its own pic_step_n
+    runs = []
+    for p, x, v in states:
+        r = pic.Run(pic.Params(npart=p.npart, ncell=p.ncell, length=p.length, dt=p.dt,
+                               history=max(64, K + 1)))
+        r.init(x, v)
+        r.step_n(16)            # capture its graph outside the timed region
+        runs.append(r)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0.record(s)
+    for r in runs:
+        r.step_n(K)
+    e1.record(s)
+    torch.cuda.synchronize()
+    t_plain = e0.elapsed_time(e1) / 1e3
+    for r in runs:
+        r.close()
+    return {"runs": len(states), "steps": K, "particles": total_particles,
+            "value": total_particles * K / t_batched, "unit": "particle-steps/s",
+            "seconds": t_batched, "plain_value": total_particles * K / t_plain,
+            "plain_seconds": t_plain, "speedup_vs_plain": t_plain / t_batched,
+            "launch": {"variant": best[0], "cluster": best[1], "block": best[2]},
+            "tune": [[list(c), round(ms, 3)] for c, ms in table[:6]]}
+
+
 def time_oracle(w, x32, v32, budget_s=12.0, sample=None, steps=None):
     """The FP64 oracle, single thread, on the same state (or its first
     `sample` particles): particle-steps/s."""
@@ -303,6 +404,7 @@ def main():
     x32, v32 = make_state(w)
     res = time_ours(args, w, x32, v32)
     e2e = None if args.no_e2e else time_e2e(args, w, x32, v32)
+    batched = None if args.no_batched else time_batched(args)
 
     n, K = w["npart"], res["steps"]
     total_s = res["total_ms"] / 1e3
@@ -350,6 +452,8 @@ def main():
                        "d2h_bytes_per_step": e2e["d2h_per_step"]}
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if batched is not None:
+        line["batched"] = batched
     print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -197,6 +197,33 @@ int pic_device_arrays(pic_run *run, void **x, void **v, void **E32);
 int pic_launch_shape(const pic_run *run, int32_t *grid, int32_t *block,
                      int32_t *variant);
 
+/* Device-side initial loading of a two-stream plasma (Sec. 2 "initialization",
+ * the Appendix A set-up, the Sec. 4 beams).  Particle j of N:
+ *   x = (j + 1/2) L/N - sum_m (eps_m/k_m) sin(k_m x0 + phase_m), k_m = 2 pi m/L,
+ *       folded into [0, L), float32 (a value rounding to L is 0);
+ *   v = s_j v0 + vth sqrt(-2 ln u1) cos(2 pi u2), s_j = +1 (j even) / -1 (odd),
+ *   u1 = (top24(z_{2j+1}) + 1) 2^-24, u2 = top24(z_{2j+2}) 2^-24, z_k the k-th
+ *   output of SplitMix64 seeded with `seed`. */
+#define PIC_LOAD_MAX_MODES 8
+typedef struct pic_loading {
+    double v0;               /* beam speed (0: one Maxwellian)                 */
+    double vth;              /* thermal spread                                 */
+    uint64_t seed;           /* SplitMix64 seed                                */
+    int32_t nmodes;          /* perturbed modes (0 .. PIC_LOAD_MAX_MODES)       */
+    int32_t reserved;        /* must be 0                                      */
+    int32_t mode[PIC_LOAD_MAX_MODES];   /* m >= 1                              */
+    double eps[PIC_LOAD_MAX_MODES];     /* density amplitude of mode m         */
+    double phase[PIC_LOAD_MAX_MODES];   /* phase of mode m                     */
+} pic_loading;
+
+/* Fill caller-owned device arrays x[n], v[n] (float32, 4-byte aligned) on
+ * `stream`.  Asynchronous. */
+int pic_load_two_stream(const pic_loading *ld, int64_t n, double length, void *x, void *v,
+                        void *stream);
+
+/* pic_init with the state generated on the device by pic_load_two_stream. */
+int pic_init_loaded(pic_run *run, const pic_loading *ld);
+
 /* One timed candidate of pic_autotune. */
 typedef struct pic_tune_entry {
     int32_t variant, block, unroll, grid;
@@ -212,6 +239,86 @@ typedef struct pic_tune_entry {
  * pic_solve_field. */
 int pic_autotune(pic_run *run, int32_t reps, pic_tune_entry *results,
                  int32_t max_results, int32_t *nresults);
+
+/* ------------------------------------------------------------------------
+ * Ensembles: many independent runs in one persistent launch (the batched and
+ * served forms of the same step).  A pool owns a caller-provided device arena
+ * and up to max_slots runs.  Every run's step is the step above, bit-identical
+ * in particles and field to the same run on its own (pic_create ...).  Each
+ * run needs pic_pool_run_bytes() of the arena; admission fails with
+ * PIC_ENOMEM when the arena or the slots are full.  A run is advanced only by
+ * pic_pool_advance, which launches one thread-block-cluster kernel for all
+ * runs with steps left: each cluster takes runs from a queue, largest work
+ * first, and keeps a run on chip through all of its steps of that launch.
+ * ------------------------------------------------------------------------ */
+
+typedef struct pic_pool pic_pool;
+
+typedef struct pic_pool_config {
+    int32_t max_slots;     /* runs held at once (>= 1)                         */
+    int32_t ncell_max;     /* largest NG admitted (<= PIC_NCELL_MAX)            */
+    int32_t history;       /* diagnostics rows kept per run (>= 1)              */
+    int32_t variant;       /* PIC_DEPOSIT_ATOMIC | _MATCH | _QUAD (0 = MATCH)  */
+    int32_t cluster;       /* blocks per cluster: 1, 2, 4, 8 (0 = 8)            */
+    int32_t block;         /* threads per block: 128 .. 512 (0 = 256)           */
+} pic_pool_config;
+
+/* Arena bytes one run with parameters *p takes in a pool with `history`
+ * rows (float32 particles, PIC_FP32_FIXED only). */
+int pic_pool_run_bytes(const pic_params *p, int32_t history, size_t *bytes);
+
+/* Bytes at the start of the arena for the pool's own tables. */
+int pic_pool_table_bytes(const pic_pool_config *cfg, size_t *bytes);
+
+/* Create a pool over a caller-owned device arena (256-byte aligned; kept
+ * alive until pic_pool_destroy).  Enqueues nothing. */
+int pic_pool_create(const pic_pool_config *cfg, void *arena, size_t arena_bytes,
+                    void *stream, pic_pool **out);
+void pic_pool_destroy(pic_pool *pool);
+
+/* Change the launch shape (variant, cluster, block) of later advances. */
+int pic_pool_configure(pic_pool *pool, int32_t variant, int32_t cluster, int32_t block);
+
+/* Admit a run: copy its initial state x0, v0 (host, N float32 each, positions
+ * in [0, L)) into the arena and queue its set-up (deposit + solve of E^0,
+ * done by the next advance).  It will be advanced for `steps` steps in total.
+ * *slot receives its slot.  PIC_ENOMEM: no free slot or arena space;
+ * PIC_EINVAL: bad parameters or positions. */
+int pic_pool_admit(pic_pool *pool, const pic_params *p, const void *x0, const void *v0,
+                   int64_t steps, int32_t *slot);
+
+/* pic_pool_admit with the initial state generated on the device
+ * (pic_load_two_stream) instead of copied from the host. */
+int pic_pool_admit_loaded(pic_pool *pool, const pic_params *p, const pic_loading *ld,
+                          int64_t steps, int32_t *slot);
+
+/* Advance every admitted run by min(k, steps left) steps (set-up first for
+ * newly admitted runs).  *active receives the number of runs that took part.
+ * Asynchronous. */
+int pic_pool_advance(pic_pool *pool, int64_t k, int32_t *active);
+
+/* Slots whose runs have done all their steps (host bookkeeping; the results
+ * are ready once the stream has reached the advance that finished them). */
+int pic_pool_finished(const pic_pool *pool, int32_t *slots, int32_t max, int32_t *n);
+
+/* Steps done by the run in `slot`. */
+int pic_pool_step_count(const pic_pool *pool, int32_t slot, int64_t *step);
+
+/* Results of a run (synchronise): state, field of its last step, history. */
+int pic_pool_get_state(pic_pool *pool, int32_t slot, void *x, void *v);
+int pic_pool_get_field(pic_pool *pool, int32_t slot, double *rho, double *phi, double *E,
+                       int64_t *rho_q);
+int pic_pool_diagnostics(pic_pool *pool, int32_t slot, int64_t first, int32_t count,
+                         pic_diag_row *rows);
+
+/* Free the run's arena space and slot. */
+int pic_pool_release(pic_pool *pool, int32_t slot);
+
+/* Wait for the stream and report the device error word. */
+int pic_pool_sync(pic_pool *pool);
+
+/* Arena bytes in use and free (largest free block). */
+int pic_pool_usage(const pic_pool *pool, size_t *used, size_t *largest_free);
 
 #ifdef __cplusplus
 }

@@ -92,6 +92,24 @@ _SIG = {
     "pic_launch_shape": (C.c_int, [_VP, C.POINTER(C.c_int32),
                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "pic_autotune": (C.c_int, [_VP, C.c_int32, _VP, C.c_int32, C.POINTER(C.c_int32)]),
+    "pic_load_two_stream": (C.c_int, [_VP, C.c_int64, C.c_double, _VP, _VP, _VP]),
+    "pic_init_loaded": (C.c_int, [_VP, _VP]),
+    "pic_pool_admit_loaded": (C.c_int, [_VP, _P, _VP, C.c_int64, C.POINTER(C.c_int32)]),
+    "pic_pool_run_bytes": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_size_t)]),
+    "pic_pool_table_bytes": (C.c_int, [_VP, C.POINTER(C.c_size_t)]),
+    "pic_pool_create": (C.c_int, [_VP, _VP, C.c_size_t, _VP, C.POINTER(_VP)]),
+    "pic_pool_destroy": (None, [_VP]),
+    "pic_pool_configure": (C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32]),
+    "pic_pool_admit": (C.c_int, [_VP, _P, _VP, _VP, C.c_int64, C.POINTER(C.c_int32)]),
+    "pic_pool_advance": (C.c_int, [_VP, C.c_int64, C.POINTER(C.c_int32)]),
+    "pic_pool_finished": (C.c_int, [_VP, _VP, C.c_int32, C.POINTER(C.c_int32)]),
+    "pic_pool_step_count": (C.c_int, [_VP, C.c_int32, C.POINTER(C.c_int64)]),
+    "pic_pool_get_state": (C.c_int, [_VP, C.c_int32, _VP, _VP]),
+    "pic_pool_get_field": (C.c_int, [_VP, C.c_int32, _VP, _VP, _VP, _VP]),
+    "pic_pool_diagnostics": (C.c_int, [_VP, C.c_int32, C.c_int64, C.c_int32, _VP]),
+    "pic_pool_release": (C.c_int, [_VP, C.c_int32]),
+    "pic_pool_sync": (C.c_int, [_VP]),
+    "pic_pool_usage": (C.c_int, [_VP, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
 }
 for _name, (_res, _args) in _SIG.items():
     _fn = getattr(_lib, _name)
@@ -201,6 +219,10 @@ class Run:
         x0, v0 = self._host(x0), self._host(v0)
         _check(_lib.pic_init(self._h, _VP(_ptr(x0)), _VP(_ptr(v0))), "pic_init")
 
+    def init_loaded(self, ld: Loading):
+        cl = ld.c()
+        _check(_lib.pic_init_loaded(self._h, C.byref(cl)), "pic_init_loaded")
+
     def set_state(self, x, v, step: int):
         x, v = self._host(x), self._host(v)
         _check(_lib.pic_set_state(self._h, _VP(_ptr(x)), _VP(_ptr(v)), int(step)),
@@ -283,6 +305,176 @@ class Run:
         _check(_lib.pic_launch_shape(self._h, C.byref(g), C.byref(b), C.byref(v)),
                "pic_launch_shape")
         return int(g.value), int(b.value), int(v.value)
+
+
+PIC_LOAD_MAX_MODES = 8
+
+
+class CLoading(C.Structure):
+    _fields_ = [("v0", C.c_double), ("vth", C.c_double), ("seed", C.c_uint64),
+                ("nmodes", C.c_int32), ("reserved", C.c_int32),
+                ("mode", C.c_int32 * PIC_LOAD_MAX_MODES),
+                ("eps", C.c_double * PIC_LOAD_MAX_MODES),
+                ("phase", C.c_double * PIC_LOAD_MAX_MODES)]
+
+
+@dataclass
+class Loading:
+    """Device-side two-stream loading (pic_loading): beams +-v0, spread vth,
+    SplitMix64 seed, density modes [(m, eps, phase), ...]."""
+    v0: float
+    vth: float
+    seed: int
+    modes: tuple = ()
+
+    def c(self) -> CLoading:
+        ld = CLoading()
+        ld.v0, ld.vth, ld.seed = float(self.v0), float(self.vth), int(self.seed)
+        ld.nmodes = len(self.modes)
+        ld.reserved = 0
+        for i, (m, eps, ph) in enumerate(self.modes):
+            ld.mode[i], ld.eps[i], ld.phase[i] = int(m), float(eps), float(ph)
+        return ld
+
+
+def load_two_stream(ld: Loading, n: int, length: float, x, v, stream=None):
+    """Fill device tensors x, v (float32, n each) on the device."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    cl = ld.c()
+    _check(_lib.pic_load_two_stream(C.byref(cl), int(n), float(length), _VP(x.data_ptr()),
+                                    _VP(v.data_ptr()), _VP(s.cuda_stream)),
+           "pic_load_two_stream")
+
+
+class CPoolConfig(C.Structure):
+    _fields_ = [("max_slots", C.c_int32), ("ncell_max", C.c_int32),
+                ("history", C.c_int32), ("variant", C.c_int32),
+                ("cluster", C.c_int32), ("block", C.c_int32)]
+
+
+def pool_run_bytes(p: Params, history: int) -> int:
+    n = C.c_size_t(0)
+    cp = p.c()
+    _check(_lib.pic_pool_run_bytes(C.byref(cp), int(history), C.byref(n)), "pic_pool_run_bytes")
+    return int(n.value)
+
+
+class Pool:
+    """An ensemble of independent runs advanced together by one persistent
+    cluster launch per advance (the batched and served forms)."""
+
+    def __init__(self, max_slots: int, ncell_max: int, arena_bytes: int, history: int = 256,
+                 variant: int = 0, cluster: int = 0, block: int = 0, device=None, stream=None):
+        import torch
+        self.device = torch.device(device if device is not None else "cuda")
+        self.cfg = CPoolConfig(int(max_slots), int(ncell_max), int(history), int(variant),
+                               int(cluster), int(block))
+        self.history = int(history)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=self.device)
+            h = _VP()
+            _check(_lib.pic_pool_create(C.byref(self.cfg), _VP(self.arena.data_ptr()),
+                                        int(arena_bytes), _VP(self.stream.cuda_stream),
+                                        C.byref(h)), "pic_pool_create")
+        self._h = h
+        self.params = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.pic_pool_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def configure(self, variant: int, cluster: int, block: int):
+        _check(_lib.pic_pool_configure(self._h, int(variant), int(cluster), int(block)),
+               "pic_pool_configure")
+
+    def admit(self, p: Params, x0, v0, steps: int):
+        """Slot of the admitted run, or None when the arena or slots are full."""
+        x0 = np.ascontiguousarray(x0, dtype=np.float32) if isinstance(x0, np.ndarray) else x0
+        v0 = np.ascontiguousarray(v0, dtype=np.float32) if isinstance(v0, np.ndarray) else v0
+        slot = C.c_int32(-1)
+        cp = p.c()
+        rc = _lib.pic_pool_admit(self._h, C.byref(cp), _VP(_ptr(x0)), _VP(_ptr(v0)),
+                                 int(steps), C.byref(slot))
+        if rc == PIC_ENOMEM:
+            return None
+        _check(rc, "pic_pool_admit")
+        self.params[slot.value] = p
+        return int(slot.value)
+
+    def admit_loaded(self, p: Params, ld: Loading, steps: int):
+        """Slot of a run generated on the device, or None when full."""
+        slot = C.c_int32(-1)
+        cp, cl = p.c(), ld.c()
+        rc = _lib.pic_pool_admit_loaded(self._h, C.byref(cp), C.byref(cl), int(steps),
+                                        C.byref(slot))
+        if rc == PIC_ENOMEM:
+            return None
+        _check(rc, "pic_pool_admit_loaded")
+        self.params[slot.value] = p
+        return int(slot.value)
+
+    def advance(self, k: int) -> int:
+        n = C.c_int32(0)
+        _check(_lib.pic_pool_advance(self._h, int(k), C.byref(n)), "pic_pool_advance")
+        return int(n.value)
+
+    def finished(self):
+        buf = np.zeros(int(self.cfg.max_slots), dtype=np.int32)
+        n = C.c_int32(0)
+        _check(_lib.pic_pool_finished(self._h, _VP(buf.ctypes.data), buf.size, C.byref(n)),
+               "pic_pool_finished")
+        return buf[:n.value].tolist()
+
+    def step_count(self, slot: int) -> int:
+        s = C.c_int64(0)
+        _check(_lib.pic_pool_step_count(self._h, int(slot), C.byref(s)), "pic_pool_step_count")
+        return int(s.value)
+
+    def get_state(self, slot: int, x=None, v=None):
+        n = self.params[slot].npart
+        x = np.empty(n, np.float32) if x is None else x
+        v = np.empty(n, np.float32) if v is None else v
+        _check(_lib.pic_pool_get_state(self._h, int(slot), _VP(_ptr(x)), _VP(_ptr(v))),
+               "pic_pool_get_state")
+        return x, v
+
+    def get_field(self, slot: int):
+        ng = self.params[slot].ncell
+        rho, phi, E = np.zeros(ng), np.zeros(ng), np.zeros(ng)
+        rq = np.zeros(ng, dtype=np.int64)
+        _check(_lib.pic_pool_get_field(self._h, int(slot), _VP(rho.ctypes.data),
+                                       _VP(phi.ctypes.data), _VP(E.ctypes.data),
+                                       _VP(rq.ctypes.data)), "pic_pool_get_field")
+        return dict(rho=rho, phi=phi, E=E, rho_q=rq)
+
+    def diagnostics(self, slot: int, first: int = 0, count: int | None = None):
+        if count is None:
+            count = self.step_count(slot) - first + 1
+        out = np.zeros(count, dtype=DIAG_DTYPE)
+        _check(_lib.pic_pool_diagnostics(self._h, int(slot), int(first), int(count),
+                                         _VP(out.ctypes.data)), "pic_pool_diagnostics")
+        return out
+
+    def release(self, slot: int):
+        _check(_lib.pic_pool_release(self._h, int(slot)), "pic_pool_release")
+        self.params.pop(slot, None)
+
+    def sync(self):
+        _check(_lib.pic_pool_sync(self._h), "pic_pool_sync")
+
+    def usage(self):
+        u, f = C.c_size_t(0), C.c_size_t(0)
+        _check(_lib.pic_pool_usage(self._h, C.byref(u), C.byref(f)), "pic_pool_usage")
+        return int(u.value), int(f.value)
 
 
 def header_functions(header_path: str | None = None):

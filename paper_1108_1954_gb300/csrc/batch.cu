@@ -1,0 +1,384 @@
+// batch.cu -- many independent PIC runs advanced in one persistent launch.
+//
+// The launch is a grid of thread-block clusters (C blocks each, one or more
+// clusters per GPC).  A cluster takes the next run from a work queue (an
+// atomic ticket over the runs ordered largest first, so the longest runs
+// start first) and advances it through all its steps on chip; then it takes
+// the next run.  Nothing on the data path crosses a cluster: no grid-wide
+// barrier, no global atomics.  Per step, with the run's NG nodes split into C
+// slices of P = ceil(NG/C) nodes and its particles into C contiguous parts:
+//
+//   A  each block pushes its particles (gather from its own copy of E in
+//      shared memory, kick, drift, wrap) and deposits them into its own
+//      fixed-point tile -- the same device code as the single-run push;
+//      cluster barrier;
+//   B  each block sums the C tiles over its node slice through distributed
+//      shared memory, forms R_g = N 2^24 - NG rho_q[g] and the slice sums
+//      sum R, sum g R; cluster barrier; from all slices' sums it has the
+//      prefixes the exact integer solve needs (as in field.cu) and computes
+//      E (Eq. 7 via the flux form of Eq. 6) for its slice in 128-bit integers,
+//      float64 at the last conversion; cluster barrier;
+//   C  each block copies the other slices of E into its own shared copy;
+//      block 0 reduces the slice diagnostics in rank order and writes the
+//      history rows.
+//
+// Every shared word a block reads from a peer was written before a cluster
+// barrier that the reader has passed, and is next overwritten (or its block
+// exits) only after a later barrier the reader must also reach, so three
+// barriers per step suffice.  The particles and E of a run are bit-identical to the single-run
+// path (the same operations on the same numbers; the density is an exact
+// integer).  The diagnostics sum in a different order and agree to rounding.
+#include <cooperative_groups.h>
+
+#include "field_ops.cuh"
+#include "particle_ops.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace pic {
+namespace {
+
+constexpr int kMaxNodesPerThread = 2;   // ceil(ceil(NG/C)/block) <= 2 (host-checked)
+
+// The part of a block's shared memory its peers read.
+struct Exchange {
+    i128 s0, s1;                  // slice sums of R and g R
+    double kv[2];                 // push sums (v_old v_new, v_new)
+    double diag[kDiagFields];     // slice diagnostics
+    unsigned long long cq;        // slice sum of rho_q
+    int ticket;                   // block 0: the run being processed
+};
+
+template <int VARIANT>
+__device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_group &cl,
+                          Exchange &ex, Tile &tile, float *sE, i128 *sh128, double *shd,
+                          float *shf, double *kvtot) {
+    const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
+    const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31;
+    const PushConsts c = R.pc;
+    const int ng = c.ng;
+    const bool push = a.push != 0;
+    const int steps = push ? R.steps : 1;
+    const long long step0 = *R.step;
+    const long long ntot = R.weight_total;
+
+    // E of the current step, ghost-padded; empty tile
+    for (int j = tid; j < ng + 2; j += bs) {
+        sE[j] = R.E32[j == 0 ? ng - 1 : (j == ng + 1 ? 0 : j - 1)];
+        tile.lo[j] = 0u;
+        tile.hi[j] = 0u;
+    }
+    __syncthreads();
+
+    const int P = (ng + C - 1) / C;
+    const int b0 = min(ng, r * P), b1 = min(ng, b0 + P);
+    const int kpt = (P + bs - 1) / bs;            // <= kMaxNodesPerThread
+    const int g0 = b0 + tid * kpt;                // this thread's first node
+    const long long n4 = R.n >> 2;
+    const long long qlo = n4 * r / C, qhi = n4 * (r + 1) / C;
+    float4 *x4 = reinterpret_cast<float4 *>(R.x);
+    float4 *v4 = reinterpret_cast<float4 *>(R.v);
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+
+    for (int s = 0; s < steps; s++) {
+        const bool last = s == steps - 1;
+        // ---- A: push + deposit into the own tile
+        float ke = 0.0f, mom = 0.0f;
+        for (long long q0 = qlo; q0 < qhi; q0 += bs) {
+            const long long q = q0 + tid;
+            const bool valid = q < qhi;
+            float4 xx = valid ? __ldcg(x4 + q) : zero4;
+            float4 vv = (push && valid) ? __ldcg(v4 + q) : zero4;
+            if (push && valid) {
+                push_particle(xx.x, vv.x, sE, c, ke, mom);
+                push_particle(xx.y, vv.y, sE, c, ke, mom);
+                push_particle(xx.z, vv.z, sE, c, ke, mom);
+                push_particle(xx.w, vv.w, sE, c, ke, mom);
+            }
+            deposit4<VARIANT>(tile, xx, valid, c, a.err, lane);
+            if (push && valid) {
+                __stcg(x4 + q, xx);
+                __stcg(v4 + q, vv);
+            }
+        }
+        if (r == 0 && tid < 32) {                 // the last N mod 4 particles
+            const long long i = n4 * 4 + lane;
+            const bool valid = i < R.n;
+            float xs = valid ? R.x[i] : 0.0f, vs = valid && push ? R.v[i] : 0.0f;
+            if (push && valid) push_particle(xs, vs, sE, c, ke, mom);
+            deposit_one<VARIANT>(tile, xs, valid, c, a.err, lane);
+            if (push && valid) { R.x[i] = xs; R.v[i] = vs; }
+        }
+        {
+            double kv[2] = {(double)ke, (double)mom};
+            block_sum_t<2, double>(kv, shd);
+            if (tid == 0) { ex.kv[0] = kv[0]; ex.kv[1] = kv[1]; }
+        }
+        cl.sync();                                                    // #1
+
+        // ---- B: node slice sums over the cluster's tiles
+        if (r == 0 && tid == 0) {
+            double k0 = 0.0, k1 = 0.0;
+            for (int b = 0; b < C; b++) {
+                const Exchange *pe = cl.map_shared_rank(&ex, b);
+                k0 += pe->kv[0];
+                k1 += pe->kv[1];
+            }
+            kvtot[0] = k0;
+            kvtot[1] = k1;
+        }
+        i128 Rg[kMaxNodesPerThread];
+        unsigned long long rq[kMaxNodesPerThread];
+        i128 S0 = 0, S1 = 0, Sz = 0;
+        unsigned long long cq = 0;
+#pragma unroll
+        for (int i = 0; i < kMaxNodesPerThread; i++) {
+            const int g = g0 + i;
+            unsigned long long q = 0;
+            if (i < kpt && g < b1) {
+                for (int b = 0; b < C; b++) {
+                    const unsigned *plo = cl.map_shared_rank(tile.lo, b);
+                    const unsigned *phi = cl.map_shared_rank(tile.hi, b);
+                    q += ((unsigned long long)phi[g + 1] << 32) | plo[g + 1];
+                    if (g == ng - 1) q += ((unsigned long long)phi[0] << 32) | plo[0];
+                    if (g == 0) q += ((unsigned long long)phi[ng + 1] << 32) | plo[ng + 1];
+                }
+                Rg[i] = (i128)ntot - (i128)ng * (i128)q;
+                S0 += Rg[i];
+                S1 += Rg[i] * (i128)g;
+            } else {
+                Rg[i] = 0;
+            }
+            rq[i] = q;
+            cq += q;
+        }
+        block_sum3_i128(S0, S1, Sz, sh128);
+        if (tid == 0) { ex.s0 = S0; ex.s1 = S1; }
+        cl.sync();                                                    // #2
+
+        // prefixes from the slice sums of all blocks, in rank order
+        i128 A0 = 0, B = 0, SR = 0, SS1 = 0;
+        for (int b = 0; b < C; b++) {
+            const Exchange *pe = cl.map_shared_rank(&ex, b);
+            const i128 t0 = pe->s0, t1 = pe->s1;
+            if (b < r) { A0 += t0; B += t1; }
+            SR += t0;
+            SS1 += t1;
+        }
+        const i128 SP = (i128)ng * SR - SS1;          // sum_k (NG-k) R_k
+        const i128 A1 = (i128)b0 * A0 - B;             // sum_{k<b0} (b0-k) R_k
+        // inclusive prefix of R over the slice -> P_g; exclusive prefix of P
+        i128 tsum = 0;
+#pragma unroll
+        for (int i = 0; i < kMaxNodesPerThread; i++) tsum += Rg[i];
+        i128 ttot;
+        const i128 texcl = block_inclusive_scan_i128(tsum, sh128, ttot) - tsum;
+        i128 Pg[kMaxNodesPerThread];
+        i128 run = A0 + texcl, psum = 0;
+#pragma unroll
+        for (int i = 0; i < kMaxNodesPerThread; i++) {
+            run += Rg[i];
+            Pg[i] = run;
+            if (i < kpt && g0 + i < b1) psum += run;
+        }
+        const i128 pexcl0 = block_inclusive_scan_i128(psum, sh128, ttot) - psum;
+        // M_{g0-1}: previous thread's last node, or the slice's left neighbour
+        const i128 Mlast = (i128)ng * Pg[kMaxNodesPerThread - 1] - SP;
+        i128 Mprev = shfl_up_i128(Mlast, 1);
+        __shared__ i128 wlast[32];
+        if (lane == 31) wlast[tid >> 5] = Mlast;
+        __syncthreads();
+        if (lane == 0)
+            Mprev = tid == 0 ? (b0 == 0 ? (i128)ng * SR - SP : (i128)ng * A0 - SP)
+                             : wlast[(tid >> 5) - 1];
+        NodeDiag d;
+        node_diag_reset(d);
+        i128 pex = pexcl0;
+#pragma unroll
+        for (int i = 0; i < kMaxNodesPerThread; i++) {
+            const int g = g0 + i;
+            if (i < kpt && g < b1) {
+                const i128 M = (i128)ng * Pg[i] - SP;
+                const double E = R.k_e * i128_to_f64(M + Mprev);
+                const float E32 = (float)E;
+                sE[g + 1] = E32;
+                if (g == ng - 1) sE[0] = E32;
+                if (g == 0) sE[ng + 1] = E32;
+                if (last) {
+                    const i128 sumM = (i128)ng * (A1 + pex) - (i128)g * SP;
+                    R.E64[g] = E;
+                    R.E32[g] = E32;
+                    R.phi[g] = R.k_phi * i128_to_f64(sumM);
+                    R.rho[g] = R.k_rho * i128_to_f64(Rg[i]);
+                    R.rho_q_last[g] = rq[i];
+                }
+                node_diag(d, g, ng, E, E32);
+                pex += Pg[i];
+                Mprev = M;
+            }
+        }
+        {
+            double dv[1] = {d.fe};
+            block_sum_t<1, double>(dv, shd);
+            float md[2 * PIC_NMODES];
+#pragma unroll
+            for (int m = 0; m < PIC_NMODES; m++) { md[2 * m] = d.re[m]; md[2 * m + 1] = d.im[m]; }
+            block_sum_t<2 * PIC_NMODES, float>(md, shf);
+            unsigned long long cqb = cq;
+            for (int o = 16; o > 0; o >>= 1) cqb += __shfl_down_sync(kFull, cqb, o);
+            __shared__ unsigned long long cqw[32];
+            if (lane == 0) cqw[tid >> 5] = cqb;
+            __syncthreads();
+            if (tid == 0) {
+                unsigned long long t = 0;
+                for (int w = 0; w < (bs >> 5); w++) t += cqw[w];
+                ex.cq = t;
+                ex.diag[kDiagFE] = dv[0];
+                ex.diag[kDiagKE] = 0.0;
+                ex.diag[kDiagMom] = 0.0;
+                ex.diag[kDiagCharge] = r == 0 ? R.dx * R.k_rho * i128_to_f64(SR) : 0.0;
+                for (int m = 0; m < 2 * PIC_NMODES; m++) ex.diag[kDiagModes + m] = (double)md[m];
+            }
+        }
+        cl.sync();                                                    // #3
+
+        // ---- C: the other slices of E into the own copy; history rows
+        for (int j = tid; j < ng + 2; j += bs) {
+            const int g = j == 0 ? ng - 1 : (j == ng + 1 ? 0 : j - 1);
+            const int owner = g / P;
+            if (owner != r) sE[j] = cl.map_shared_rank(sE, owner)[j];
+            tile.lo[j] = 0u;
+            tile.hi[j] = 0u;
+        }
+        if (r == 0 && tid == 0) {
+            double tot[kDiagFields];
+            for (int f = 0; f < kDiagFields; f++) tot[f] = 0.0;
+            unsigned long long cqt = 0;
+            for (int b = 0; b < C; b++) {
+                const Exchange *pe = cl.map_shared_rank(&ex, b);
+                for (int f = 0; f < kDiagFields; f++) tot[f] += pe->diag[f];
+                cqt += pe->cq;
+            }
+            long long n = step0 + s;
+            if (push) {
+                pic_diag_row *row = &R.hist[n % R.hist_len];
+                row->kinetic = 0.5 * R.mass * kvtot[0];
+                row->momentum = R.mass * kvtot[1];
+                n += 1;
+            }
+            pic_diag_row *row = &R.hist[n % R.hist_len];
+            const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+            row->step = n;
+            row->kinetic = qnan;
+            row->momentum = qnan;
+            row->field = 0.5 * R.dx * tot[kDiagFE];
+            row->charge = tot[kDiagCharge];
+            row->charge_q = (long long)cqt;
+            for (int m = 0; m < PIC_NMODES; m++) {
+                const double re = tot[kDiagModes + 2 * m], im = tot[kDiagModes + 2 * m + 1];
+                row->mode[m] = 2.0 * sqrt(re * re + im * im) / (double)ng;
+            }
+        }
+        __syncthreads();
+    }
+    if (r == 0 && tid == 0 && push) *R.step = step0 + steps;
+}
+
+template <int VARIANT>
+__global__ void __launch_bounds__(512) pic_batch_kernel(BatchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ Exchange ex;
+    __shared__ i128 sh128[96];
+    __shared__ double shd[32 * 2];
+    __shared__ float shf[32 * 2 * PIC_NMODES];
+    __shared__ double kvtot[2];
+    cg::cluster_group cl = cg::this_cluster();
+    const int ngm = a.ng_max;
+    Tile tile;
+    tile.lo = reinterpret_cast<unsigned *>(smem_raw);
+    tile.hi = tile.lo + ngm + 2;
+    tile.packed = nullptr;
+    float *sE = reinterpret_cast<float *>(tile.hi + ngm + 2);
+    for (;;) {
+        if (cl.block_rank() == 0 && threadIdx.x == 0) ex.ticket = (int)atomicAdd(a.next, 1u);
+        cl.sync();
+        const int ticket = *cl.map_shared_rank(&ex.ticket, 0);
+        // every block has read block 0's ticket before block 0 may overwrite
+        // it or exit (a block's shared memory must not be read after it exits)
+        cl.sync();
+        if (ticket >= a.nrun) break;
+        const BatchRun R = a.runs[a.order[ticket]];
+        if (!(a.push && R.steps == 0))
+            run_steps<VARIANT>(a, R, cl, ex, tile, sE, sh128, shd, shf, kvtot);
+        cl.sync();
+    }
+}
+
+using BatchKernel = void (*)(BatchArgs);
+
+BatchKernel pick_batch(int variant) {
+    switch (variant) {
+        case PIC_DEPOSIT_ATOMIC: return &pic_batch_kernel<PIC_DEPOSIT_ATOMIC>;
+        case PIC_DEPOSIT_MATCH: return &pic_batch_kernel<PIC_DEPOSIT_MATCH>;
+        case PIC_DEPOSIT_QUAD: return &pic_batch_kernel<PIC_DEPOSIT_QUAD>;
+        default: return nullptr;
+    }
+}
+
+}  // namespace
+
+size_t batch_smem_bytes(int ng_max, int cluster, int block) {
+    (void)cluster;
+    (void)block;
+    return (size_t)(ng_max + 2) * 12;
+}
+
+cudaError_t batch_prepare_attributes() {
+    const int bytes = (int)batch_smem_bytes(PIC_NCELL_MAX, 8, 512);
+    const int vs[3] = {PIC_DEPOSIT_ATOMIC, PIC_DEPOSIT_MATCH, PIC_DEPOSIT_QUAD};
+    for (int v : vs) {
+        cudaError_t e = cudaFuncSetAttribute(pick_batch(v),
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+static void batch_config(cudaLaunchConfig_t &cfg, cudaLaunchAttribute *attr, int cluster,
+                         int block, int nclusters, size_t smem, cudaStream_t s) {
+    cfg = cudaLaunchConfig_t{};
+    cfg.gridDim = dim3((unsigned)(cluster * nclusters));
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+}
+
+int batch_max_clusters(int variant, int cluster, int block, int ng_max) {
+    BatchKernel k = pick_batch(variant);
+    if (!k) return 0;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    batch_config(cfg, attr, cluster, block, 1, batch_smem_bytes(ng_max, cluster, block), nullptr);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess) return 0;
+    return n;
+}
+
+cudaError_t launch_batch(const BatchArgs &a, int variant, int cluster, int block,
+                         int nclusters, cudaStream_t s) {
+    BatchKernel k = pick_batch(variant);
+    if (!k) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    batch_config(cfg, attr, cluster, block, nclusters,
+                 batch_smem_bytes(a.ng_max, cluster, block), s);
+    return cudaLaunchKernelEx(&cfg, k, a);
+}
+
+}  // namespace pic

@@ -35,6 +35,60 @@ __device__ __forceinline__ double i128_to_f64(i128 v) {
 }
 
 
+// Inclusive scan of one i128 per thread over the block; returns the inclusive
+// value and the block total.  sh must hold 33 entries.
+static __device__ i128 block_inclusive_scan_i128(i128 v, i128 *sh, i128 &total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+        const i128 t = shfl_up_i128(v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) sh[w] = v;
+    __syncthreads();
+    i128 off = 0, tot = 0;
+    for (int i = 0; i < nw; i++) {
+        if (i < w) off += sh[i];
+        tot += sh[i];
+    }
+    __syncthreads();
+    total = tot;
+    return v + off;
+}
+
+// Sum of three i128 values over the block (all threads get the sums).
+static __device__ void block_sum3_i128(i128 &a, i128 &b, i128 &c, i128 *sh /*[96]*/) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        a += shfl_down_i128(a, o);
+        b += shfl_down_i128(b, o);
+        c += shfl_down_i128(c, o);
+    }
+    if (lane == 0) { sh[w] = a; sh[32 + w] = b; sh[64 + w] = c; }
+    __syncthreads();
+    a = 0; b = 0; c = 0;
+    for (int i = 0; i < nw; i++) { a += sh[i]; b += sh[32 + i]; c += sh[64 + i]; }
+    __syncthreads();
+}
+
+// Block sum of K doubles, fixed order; result valid in thread 0.
+template <int K, typename T>
+static __device__ void block_sum_t(T (&v)[K], T *sh /*[32*K]*/) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int i = 0; i < K; i++)
+        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(kFull, v[i], o);
+    if (lane == 0)
+        for (int i = 0; i < K; i++) sh[w * K + i] = v[i];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int i = 0; i < K; i++) {
+            T s = 0;
+            for (int j = 0; j < nw; j++) s += sh[j * K + i];
+            v[i] = s;
+        }
+    __syncthreads();
+}
+
 // Per-node diagnostics contribution of node g with field E (float64) and its
 // float32 copy: field energy sum and the mode sums (float32 twiddles).
 struct NodeDiag {

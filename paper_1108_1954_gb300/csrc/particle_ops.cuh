@@ -10,6 +10,14 @@
 
 namespace pic {
 
+using u64 = unsigned long long;
+constexpr int kMatchPacked = PIC_DEPOSIT_MATCH_PACKED;
+constexpr unsigned long long kPackShift = 40;
+constexpr unsigned long long kPackMask = (1ull << kPackShift) - 1ull;
+// particles a block may pack into one node between flushes
+constexpr int kPackLimit = 65535 - 32;
+
+
 // Cell location of a float32 position by the fixed-point recipe:
 //   s = x*c - 1/2, fl = floor(s), f = s - fl   (float ops, round to nearest)
 // floor(s) is formed as (s + 1.5*2^23 rounded down) - 1.5*2^23, which equals
@@ -62,6 +70,97 @@ __device__ __forceinline__ void push_particle(float &x, float &v, const float *s
     xn = xn >= c.length ? 0.0f : xn;   // x + L rounded up to L: the point 0
     x = xn;
     v = vn;
+}
+
+// Shared-memory density tiles.  GB300 has no single-instruction 64-bit
+// integer add on shared memory (it runs as a compare-and-swap loop, which
+// serialises badly when the lanes of a warp hit one node), so the unpacked
+// variants keep each node's 64-bit sum as two 32-bit words: a 32-bit
+// fetch-add on the low word, and +1 on the high word from the one add that
+// wraps it.  The packed variants keep one 64-bit word per left node
+// (count << 40 | sum W) and use the 64-bit add.
+// Both tiles are ghost-padded: index j is node (j-1) mod NG, j = 0..NG+1.
+struct Tile {
+    unsigned *lo, *hi;      // unpacked: 32-bit halves of the node sums
+    u64 *packed;            // packed: one word per left node
+};
+
+__device__ __forceinline__ void tile_add(const Tile &t, unsigned j, unsigned val) {
+    const unsigned old = atomicAdd(&t.lo[j], val);
+    if (old + val < old) atomicAdd(&t.hi[j], 1u);
+}
+
+// Deposit one particle (all 32 lanes of the warp call this together for the
+// MATCH variants).
+template <int VARIANT>
+__device__ __forceinline__ void deposit_one(const Tile &t, float x, bool valid,
+                                            const PushConsts &c, unsigned *err, int lane) {
+    const Loc l = locate(x, c.inv_dx);
+    const bool ok = valid && l.j <= (unsigned)c.ng;
+    if (valid && !ok) atomicOr(err, kErrPosition);
+    const unsigned W = ok ? fixed_weight(l.f) : 0u;
+    if (VARIANT == PIC_DEPOSIT_ATOMIC || VARIANT == PIC_DEPOSIT_QUAD) {
+        if (ok) {
+            tile_add(t, l.j, kFixOne - W);
+            tile_add(t, l.j + 1, W);
+        }
+    } else if (VARIANT == PIC_DEPOSIT_PACKED) {
+        if (ok) atomicAdd(&t.packed[l.j], (1ull << kPackShift) | (u64)W);
+    } else {
+        const unsigned key = ok ? l.j : 0xffffffffu;
+        const unsigned peers = __match_any_sync(kFull, key);
+        const unsigned wsum = __reduce_add_sync(peers, W);
+        if (ok && lane == __ffs(peers) - 1) {
+            const unsigned cnt = (unsigned)__popc(peers);
+            if (VARIANT == PIC_DEPOSIT_MATCH) {
+                // cnt * 2^24 - wsum <= 2^29: fits the 32-bit add
+                tile_add(t, l.j, (cnt << kFixBits) - wsum);
+                tile_add(t, l.j + 1, wsum);
+            } else {
+                atomicAdd(&t.packed[l.j], ((u64)cnt << kPackShift) + (u64)wsum);
+            }
+        }
+    }
+}
+
+// Deposit the 4 particles of a float4 group (valid per lane).
+template <int VARIANT>
+__device__ __forceinline__ void deposit4(const Tile &t, const float4 &xx, bool valid,
+                                         const PushConsts &c, unsigned *err, int lane) {
+    const float xs[4] = {xx.x, xx.y, xx.z, xx.w};
+    if (VARIANT == PIC_DEPOSIT_QUAD) {
+        // consecutive particles of the group with equal left node are summed
+        // in registers first (at most 4 * 2^24 per word), then added once
+        unsigned key = 0xffffffffu, left = 0, right = 0;
+        bool bad = false;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const Loc l = locate(xs[k], c.inv_dx);
+            const bool ok = valid && l.j <= (unsigned)c.ng;
+            bad |= valid && !ok;
+            const unsigned W = fixed_weight(l.f);
+            if (ok && l.j == key) {
+                left += kFixOne - W;
+                right += W;
+            } else if (ok) {
+                if (key != 0xffffffffu) {
+                    tile_add(t, key, left);
+                    tile_add(t, key + 1, right);
+                }
+                key = l.j;
+                left = kFixOne - W;
+                right = W;
+            }
+        }
+        if (key != 0xffffffffu) {
+            tile_add(t, key, left);
+            tile_add(t, key + 1, right);
+        }
+        if (bad) atomicOr(err, kErrPosition);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; k++) deposit_one<VARIANT>(t, xs[k], valid, c, err, lane);
+    }
 }
 
 }  // namespace pic

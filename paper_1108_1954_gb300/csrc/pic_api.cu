@@ -28,7 +28,9 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
-int validate(const pic_params *p) {
+}  // namespace
+
+int pic::validate_params(const pic_params *p) {
     if (!p) return PIC_EINVAL;
     if (p->npart < 1 || p->npart > (int64_t)0xFFFFFFFFll) return PIC_EINVAL;
     if (p->ncell < 1 || p->ncell > PIC_NCELL_MAX) return PIC_EINVAL;
@@ -43,6 +45,8 @@ int validate(const pic_params *p) {
     if (p->unroll != 0 && p->unroll != 1 && p->unroll != 2 && p->unroll != 4) return PIC_EINVAL;
     return PIC_OK;
 }
+
+namespace {
 
 struct Layout {
     size_t x[2], v[2];
@@ -326,15 +330,8 @@ int read_error_word(pic_run *r) {
     return err ? PIC_EDEVICE : PIC_OK;
 }
 
-// Upload a state, deposit it and solve: E^step ready.
-int load_state(pic_run *r, const void *x, const void *v, int64_t step) {
-    if (!x || !v) return PIC_EINVAL;
-    int rc = check_host_positions(r, x);
-    if (rc) return rc;
-    const size_t bytes = (size_t)r->p.npart * r->elem();
-    r->cur = 0;
-    PIC_CUDA(cudaMemcpyAsync(r->xs(0), x, bytes, cudaMemcpyHostToDevice, r->stream));
-    PIC_CUDA(cudaMemcpyAsync(r->vs(0), v, bytes, cudaMemcpyHostToDevice, r->stream));
+// With x, v in buffer 0: reset the run, deposit and solve: E^step ready.
+int prepare_loaded(pic_run *r, int64_t step) {
     DevScalars ds{};
     ds.step = step;
     PIC_CUDA(cudaMemcpyAsync(r->dev(), &ds, sizeof(ds), cudaMemcpyHostToDevice, r->stream));
@@ -349,6 +346,18 @@ int load_state(pic_run *r, const void *x, const void *v, int64_t step) {
     r->ready = true;
     r->pending_push = false;
     return read_error_word(r);
+}
+
+// Upload a state, deposit it and solve: E^step ready.
+int load_state(pic_run *r, const void *x, const void *v, int64_t step) {
+    if (!x || !v) return PIC_EINVAL;
+    int rc = check_host_positions(r, x);
+    if (rc) return rc;
+    const size_t bytes = (size_t)r->p.npart * r->elem();
+    r->cur = 0;
+    PIC_CUDA(cudaMemcpyAsync(r->xs(0), x, bytes, cudaMemcpyHostToDevice, r->stream));
+    PIC_CUDA(cudaMemcpyAsync(r->vs(0), v, bytes, cudaMemcpyHostToDevice, r->stream));
+    return prepare_loaded(r, step);
 }
 
 }  // namespace
@@ -371,7 +380,7 @@ const char *pic_strerror(int code) {
 }
 
 int pic_workspace_size(const pic_params *p, size_t *bytes) {
-    int rc = validate(p);
+    int rc = validate_params(p);
     if (rc) return rc;
     if (!bytes) return PIC_EINVAL;
     Layout L;
@@ -384,7 +393,7 @@ int pic_create(const pic_params *p, void *workspace, size_t workspace_bytes,
                void *stream, pic_run **out) {
     if (!out) return PIC_EINVAL;
     *out = nullptr;
-    int rc = validate(p);
+    int rc = validate_params(p);
     if (rc) return rc;
     if (!workspace || ((uintptr_t)workspace % kAlign)) return PIC_EINVAL;
     pic_run *r = new (std::nothrow) pic_run();
@@ -417,7 +426,7 @@ int pic_create(const pic_params *p, void *workspace, size_t workspace_bytes,
     r->k_phi = -r->dx * r->dx * r->k_rho / (double)p->ncell;
 
     // launch shape of the fused push
-    r->variant = p->deposit_variant ? p->deposit_variant : PIC_DEPOSIT_PACKED;
+    r->variant = p->deposit_variant ? p->deposit_variant : PIC_DEPOSIT_ATOMIC;
     if (p->precision != PIC_FP32_FIXED) r->variant = PIC_DEPOSIT_ATOMIC;
     r->block = p->block_size ? p->block_size : 256;
     r->unroll = p->unroll ? p->unroll : 1;
@@ -439,6 +448,18 @@ void pic_destroy(pic_run *run) {
 int pic_init(pic_run *run, const void *x0, const void *v0) {
     if (!run) return PIC_EINVAL;
     return load_state(run, x0, v0, 0);
+}
+
+int pic_init_loaded(pic_run *run, const pic_loading *ld) {
+    if (!run || !ld) return PIC_EINVAL;
+    if (run->p.precision == PIC_FP64) return PIC_EINVAL;
+    LoadArgs a;
+    int rc = make_load_args(ld, run->p.npart, run->p.length, (float *)run->xs(0),
+                            (float *)run->vs(0), &a);
+    if (rc) return rc;
+    run->cur = 0;
+    PIC_CUDA(launch_load(a, run->sms, run->stream));
+    return prepare_loaded(run, 0);
 }
 
 int pic_set_state(pic_run *run, const void *x, const void *v, int64_t step) {

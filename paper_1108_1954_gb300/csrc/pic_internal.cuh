@@ -119,6 +119,50 @@ struct SortArgs {
     unsigned int *err;
 };
 
+// One run of a batched ensemble (device descriptor; host-built).
+struct BatchRun {
+    float *x, *v;                 // particles, 16-byte aligned
+    long long n;                  // N
+    PushConsts pc;                // ng, c = NG/L, L, qm dt, dt (float32)
+    float *E32;                   // [NG] field of the current step (state)
+    double *E64, *phi, *rho;      // [NG] written at the end of a launch
+    unsigned long long *rho_q_last;  // [NG] idem
+    pic_diag_row *hist;           // history ring of the run
+    int hist_len;
+    int steps;                    // steps to advance in this launch (0: idle)
+    long long *step;              // device step counter of the run
+    long long weight_total;       // N 2^24
+    double k_rho, k_e, k_phi, dx, mass;
+};
+
+struct BatchArgs {
+    BatchRun *runs;
+    const int *order;             // runs to process, largest first
+    int nrun;                     // entries of order
+    unsigned *next;               // work-queue ticket (0 at launch)
+    unsigned *err;                // device error word
+    int push;                     // 1: advance `steps`; 0: deposit + solve only
+    int ng_max;                   // largest NG of the launch (tile size)
+};
+
+// Device-side initial loading (load.cu).
+struct LoadArgs {
+    float *x, *v;
+    long long n;
+    double length;
+    float lengthf;
+    float v0, vth;
+    unsigned long long seed;
+    int nmodes;
+    float k[PIC_LOAD_MAX_MODES], amp[PIC_LOAD_MAX_MODES], phase[PIC_LOAD_MAX_MODES];
+};
+cudaError_t launch_load(const LoadArgs &a, int sms, cudaStream_t s);
+int make_load_args(const pic_loading *ld, long long n, double length, float *x, float *v,
+                   LoadArgs *out);
+
+// Parameter checks shared by the single-run and the pool entry points.
+int validate_params(const pic_params *p);
+
 // Launchers (each returns the launch's cudaError_t).
 cudaError_t launch_push_fixed(const PushArgs &a, int grid, int block,
                               int variant, int unroll, bool push, cudaStream_t s);
@@ -139,5 +183,11 @@ cudaError_t launch_sort_f32(const SortArgs<float> &a, cudaStream_t s);
 cudaError_t launch_sort_f64(const SortArgs<double> &a, cudaStream_t s);
 cudaError_t sort_prepare_attributes(int ng);
 constexpr int kSortThreads = 256;
+
+cudaError_t launch_batch(const BatchArgs &a, int variant, int cluster, int block,
+                         int nclusters, cudaStream_t s);
+size_t batch_smem_bytes(int ng_max, int cluster, int block);
+int batch_max_clusters(int variant, int cluster, int block, int ng_max);
+cudaError_t batch_prepare_attributes();
 
 }  // namespace pic
