@@ -41,6 +41,10 @@ C2 = dict(npart=1 << 26, ncell=4096, length=4.0 * math.pi, dt=0.1, v0=0.2,
           vth=0.01, eps=1e-4, sort_interval=20, seed=2026)
 SMALL = dict(npart=1 << 20, ncell=4096, length=4.0 * math.pi, dt=0.1, v0=0.2,
              vth=0.01, eps=1e-4, sort_interval=20, seed=2026)
+# the config-2 recipe at 2^25 particles: the profiling case (256 MiB of
+# particles, above L2, a few GB on the device at most)
+PROFILE = dict(npart=1 << 25, ncell=4096, length=4.0 * math.pi, dt=0.1, v0=0.2,
+               vth=0.01, eps=1e-4, sort_interval=20, seed=2026)
 REF_SAMPLE = 1 << 20
 
 
@@ -50,7 +54,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "small"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "small", "profile"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--variant", type=int, default=0)
@@ -61,11 +65,18 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-runs", type=int, default=512)
     ap.add_argument("--batched-steps", type=int, default=500)
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--serve-advance", type=int, default=50)
+    ap.add_argument("--precision", action="store_true",
+                    help="add the precision study (config 4)")
+    ap.add_argument("--precision-steps", type=int, default=2000)
+    ap.add_argument("--precision-oracle-steps", type=int, default=150)
     return ap.parse_args()
 
 
 def workload(name):
-    return dict(C2) if name == "c2" else dict(SMALL)
+    return dict({"c2": C2, "small": SMALL, "profile": PROFILE}[name])
 
 
 def make_state(w):
@@ -346,6 +357,78 @@ def time_batched(args):
             "tune": [[list(c), round(ms, 3)] for c, ms in table[:6]]}
 
 
+def precision_study(args):
+    """Config 4: 2^24 electrons, 1024 cells, beams +-0.2 with vth 0.02 seeded
+    with the growing mode-1 eigenmode, run in the three precision modes; the
+    FP64 oracle runs the same state for a bounded window."""
+    import numpy as np
+    import oracle as O
+    import workloads as W
+    import paper_1108_1954_gb300 as pic
+    n, ng, L, K = 1 << 24, 1024, 4.0 * math.pi, args.precision_steps
+    x, v = W.two_stream_eigenmode(n, L, 0.2, 0.02, 1e-3, 1, 4)
+    x32, v32 = W.to_f32_state(x, v, L)
+    dt = 0.1
+    t = np.arange(K) * dt
+    fit = (t >= 2.0) & (t <= 12.0)
+    m = L / n
+    out = {"npart": n, "ncell": ng, "steps": K, "gamma_theory": W.cold_two_stream_gamma(2 * math.pi / L, 0.2)}
+    ref = O.State(O.params(ng, n, L, dt), x32.astype(np.float64), v32.astype(np.float64))
+    t0 = time.perf_counter()
+    h = ref.run(args.precision_oracle_steps)
+    o_fe = h[:, 2]
+    o_ke = 0.5 * ref.mass * h[:, 0]
+    ko = args.precision_oracle_steps
+    fo = fit[:ko]
+    o_gamma = float(np.polyfit(t[:ko][fo], np.log(h[fo, 3]), 1)[0]) if fo.sum() > 4 else None
+    out["oracle"] = {"steps": ko, "seconds": time.perf_counter() - t0, "gamma1": o_gamma}
+    for name, mode, xs, vs in (("fp64", pic.PIC_FP64, x, v),
+                               ("fp32_atomic", pic.PIC_FP32_ATOMIC, x32, v32),
+                               ("fp32_fixed", pic.PIC_FP32_FIXED, x32, v32)):
+        run = pic.Run(pic.Params(npart=n, ncell=ng, length=L, dt=dt, precision=mode,
+                                 history=K + 1, sort_interval=20))
+        run.init(xs, vs)
+        t0 = time.perf_counter()
+        run.step_n(K)
+        run.sync()
+        el = time.perf_counter() - t0
+        d = run.diagnostics(0, K)
+        run.close()
+        tot = d["kinetic"] + d["field"]
+        vabs = m * np.abs(np.asarray(vs, np.float64)).sum()
+        g1 = float(np.polyfit(t[fit], np.log(d["mode"][fit, 0]), 1)[0])
+        kk = min(ko, K)
+        out[name] = {
+            "seconds": el, "particle_steps_per_s": n * K / el,
+            "energy_drift": float((tot.max() - tot.min()) / tot[0]),
+            "momentum_error": float(np.abs(d["momentum"] - d["momentum"][0]).max() / vabs),
+            "gamma1": g1,
+            "gamma1_vs_oracle": (g1 - o_gamma) / o_gamma if o_gamma else None,
+            "field_energy_vs_oracle": float(np.abs(d["field"][:kk] - o_fe[:kk]).max() / o_fe[:kk].max()),
+            "kinetic_vs_oracle": float(np.abs(d["kinetic"][:kk] - o_ke[:kk]).max() / o_ke[:kk].max()),
+        }
+    return out
+
+
+def time_served(args):
+    """Config 5: Poisson arrivals (mean 200/s) of run requests served by the
+    continuous-batching loop within a 150 GB device-memory budget."""
+    import workloads as W
+    import paper_1108_1954_gb300 as pic
+    from paper_1108_1954_gb300 import serve
+    stream = W.request_stream(args.serve_requests, 200.0, 11)
+    reqs = serve.requests_from_stream(stream,
+                                      modes_fn=lambda r: W.two_stream_modes_1_to_8(1e-4, r["seed"]))
+    budget = 150 * (1 << 30)
+    srv = serve.Server(arena_bytes=budget, max_slots=2048, ncell_max=4096, history=8,
+                       advance_steps=args.serve_advance, variant=2, cluster=8, block=256)
+    _, stats = srv.serve(reqs)
+    srv.close()
+    stats.update({"unit": "particle-steps/s", "budget_bytes": budget,
+                  "arrival_rate_per_s": 200.0})
+    return stats
+
+
 def time_oracle(w, x32, v32, budget_s=12.0, sample=None, steps=None):
     """The FP64 oracle, single thread, on the same state (or its first
     `sample` particles): particle-steps/s."""
@@ -405,6 +488,8 @@ def main():
     res = time_ours(args, w, x32, v32)
     e2e = None if args.no_e2e else time_e2e(args, w, x32, v32)
     batched = None if args.no_batched else time_batched(args)
+    served = None if args.no_served else time_served(args)
+    precision = precision_study(args) if (args.precision and rank == 0) else None
 
     n, K = w["npart"], res["steps"]
     total_s = res["total_ms"] / 1e3
@@ -454,6 +539,10 @@ def main():
         line["cpu_baseline"] = cpu
     if batched is not None:
         line["batched"] = batched
+    if served is not None:
+        line["served"] = served
+    if precision is not None:
+        line["precision"] = precision
     print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -74,12 +74,13 @@ def assert_same(pool, slot, ref, steps):
     np.testing.assert_allclose(ds["mode"], d["mode"], rtol=1e-4, atol=1e-6 * max(1e-300, np.abs(d["mode"]).max()))
 
 
-@pytest.mark.parametrize("variant,cluster,block", [(2, 8, 256), (1, 8, 256), (5, 4, 256),
-                                                   (2, 2, 512), (2, 1, 256)])
-def test_batched_equals_alone(variant, cluster, block):
-    runs = run_set()
+@pytest.mark.parametrize("variant,cluster,block,ncell_max",
+                         [(2, 8, 256, 2048), (1, 8, 256, 2048), (5, 4, 256, 2048),
+                          (2, 2, 512, 2048), (2, 1, 512, 1024), (1, 4, 128, 1024)])
+def test_batched_equals_alone(variant, cluster, block, ncell_max):
+    runs = [r for r in run_set() if r[0].ncell <= ncell_max]
     steps = 23
-    pool = pic.Pool(max_slots=16, ncell_max=2048, arena_bytes=GIB, history=512,
+    pool = pic.Pool(max_slots=16, ncell_max=ncell_max, arena_bytes=GIB, history=512,
                     variant=variant, cluster=cluster, block=block, device="cuda:0")
     slots = [pool.admit(p, x, v, steps) for p, x, v in runs]
     assert None not in slots
@@ -119,9 +120,9 @@ def test_admission_by_memory_and_slots():
     assert per >= 8 * 100000
     x, v = W.two_stream(100000, L4PI, 0.2, 0.01, 3)
     x32, v32 = W.to_f32_state(x, v, L4PI)
-    # room for the tables and exactly two runs
-    pool = pic.Pool(max_slots=4, ncell_max=256, arena_bytes=2 * per + (1 << 20), history=64,
-                    device="cuda:0")
+    # room for the tables (a few KB for 4 slots) and exactly two runs
+    pool = pic.Pool(max_slots=4, ncell_max=256, arena_bytes=2 * per + per // 2 + 4096,
+                    history=64, device="cuda:0")
     a = pool.admit(p, x32, v32, 5)
     b = pool.admit(p, x32, v32, 5)
     assert a is not None and b is not None

@@ -1,0 +1,77 @@
+"""The precision-study modes against the FP64 oracle: the float64 push and
+deposit (PIC_FP64) to rounding, the float32 push with a float32 atomic
+deposit (PIC_FP32_ATOMIC) within float32 bounds."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1108_1954_gb300 as pic  # noqa: E402
+import torch  # noqa: E402,F401
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+L4PI = 4.0 * math.pi
+
+
+def periodic_dist(a, b, L):
+    d = np.abs(np.asarray(a, np.float64) - np.asarray(b, np.float64))
+    return np.minimum(d, L - d)
+
+
+@pytest.mark.parametrize("n,ng", [(20000, 64), (100003, 1024)])
+def test_fp64_mode_one_step(n, ng):
+    x, v = W.two_stream(n, L4PI, 0.2, 0.02, 7 + n)
+    run = pic.Run(pic.Params(npart=n, ncell=ng, length=L4PI, precision=pic.PIC_FP64),
+                  device="cuda:0")
+    run.init(x, v)
+    ref = O.State(O.params(ng, n, L4PI, 0.1), x, v)
+    f0 = run.get_field()
+    assert np.abs(f0["rho"] - ref.rho).max() <= 1e-12
+    assert np.abs(f0["E"] - ref.E).max() <= 1e-10 * np.abs(ref.E).max()
+    for _ in range(3):
+        run.step_n(1)
+        ref.step()
+    x1, v1 = run.get_state()
+    assert periodic_dist(x1, ref.x, L4PI).max() <= 1e-12 * L4PI
+    assert np.abs(v1 - ref.v).max() <= 1e-12
+    f = run.get_field()
+    assert np.abs(f["E"] - ref.E).max() <= 1e-10 * np.abs(ref.E).max()
+
+
+def test_fp32_atomic_mode_one_step():
+    n, ng = 100003, 512
+    x, v = W.two_stream(n, L4PI, 0.2, 0.02, 3)
+    x32, v32 = W.to_f32_state(x, v, L4PI)
+    run = pic.Run(pic.Params(npart=n, ncell=ng, length=L4PI, precision=pic.PIC_FP32_ATOMIC),
+                  device="cuda:0")
+    run.init(x32, v32)
+    ref = O.State(O.params(ng, n, L4PI, 0.1), x32.astype(np.float64), v32.astype(np.float64))
+    f0 = run.get_field()
+    # a node's float32 sum of ~2N/NG weights (each <= 1) is off by at most
+    # (2N/NG) * (N/NG) * 2^-24, i.e. 2 (N/NG) 2^-24 in rho after the Q0/dx
+    # scale (NG/N); the float32 fraction adds ~sqrt(NG/N) NG 2^-24 (as in the
+    # fixed-point mode)
+    tol = 4 * (n / ng) * 2.0 ** -24 + 16 * math.sqrt(ng / n) * ng * 2.0 ** -24
+    assert np.abs(f0["rho"] - ref.rho).max() <= tol
+    run.push()
+    run.solve_field()
+    ref.step()
+    x1, v1 = run.get_state()
+    assert periodic_dist(x1, ref.x, L4PI).max() <= 1e-5 * L4PI
+    assert (np.abs(v1 - ref.v) <= 1e-5 * np.maximum(np.abs(ref.v), 0.22)).all()
+
+
+def test_fp64_mode_conservation_and_sort():
+    n = 20000
+    x, v = W.two_stream(n, L4PI, 0.2, 0.01, 11)
+    run = pic.Run(pic.Params(npart=n, ncell=64, length=L4PI, precision=pic.PIC_FP64,
+                             sort_interval=20), device="cuda:0")
+    run.init(x, v)
+    run.step_n(200)
+    d = run.diagnostics(0, 200)
+    tot = d["kinetic"] + d["field"]
+    assert (tot.max() - tot.min()) / tot[0] < 0.01
+    m = L4PI / n
+    assert np.abs(d["momentum"] - d["momentum"][0]).max() <= 1e-10 * m * np.abs(v).sum()
