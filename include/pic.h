@@ -167,6 +167,30 @@ int pic_step_n(pic_run *run, int64_t n);
 /* Wait for the stream, then report the device error word (PIC_EDEVICE). */
 int pic_sync(pic_run *run);
 
+/* The counting sort by cell of pic_sort, for callers that cannot allocate
+ * device memory.  The paper has no counterpart; this is a service of the
+ * library.  Some callers cannot hand the library a workspace: a framework
+ * whose own caching allocator owns all of the device memory and takes no
+ * outside allocations, a process held to a fixed memory reservation, or
+ * latency-critical code that cannot pay for the device-wide synchronisation a
+ * cudaMalloc brings.  This entry point allocates nothing: its scratch (cell
+ * counts, offsets, cell bases, an error word) lives in one device array of
+ * PIC_SORT_NOALLOC_SCRATCH bytes inside the library, which every GPU that
+ * loads the library keeps until the process exits.
+ * x, v: n float32 positions and velocities (device memory); x_out, v_out:
+ * n float32 each (device memory, not the inputs), receiving the particles
+ * ordered by cell trunc(x NG/L) (clamped to [0, NG-1]), particles of one cell
+ * in their input order.  Limits: 1 <= n <= 2^32 - 1, 1 <= ncell <=
+ * PIC_NCELL_MAX, else PIC_EINVAL; larger n only uses fewer, longer chunks to
+ * keep the tables inside the array.  Enqueued on `stream`, asynchronous.  The
+ * first call on a device looks up the array's device address with that device
+ * current: make it before any stream capture.  Every call shares the array and
+ * leaves its contents behind (each call rewrites its tables in full and clears
+ * the error word first); calls whose work overlaps on the GPU race on it. */
+#define PIC_SORT_NOALLOC_SCRATCH (4u << 20)
+int pic_sort_noalloc(const float *x, const float *v, float *x_out, float *v_out, int64_t n,
+                     int32_t ncell, double length, void *stream);
+
 /* Copy the diagnostics rows of steps [first, first + count) (each must still
  * be in the history ring) to rows[] on the host.  Synchronises. */
 int pic_diagnostics(pic_run *run, int64_t first, int32_t count,
