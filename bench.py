@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--batched-runs", type=int, default=512)
     ap.add_argument("--batched-steps", type=int, default=500)
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--only-batched", action="store_true",
+                    help="run only the batched-ensemble section (profiling)")
+    ap.add_argument("--no-tune-batched", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-advance", type=int, default=50)
     ap.add_argument("--precision", action="store_true",
@@ -158,9 +161,13 @@ def recorded_traffic():
         rec = json.load(open(path))
     except (OSError, ValueError):
         return None
-    src = os.path.join(ROOT, "paper_1108_1954_gb300", "csrc", "push.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if rec.get("push_cu_sha256") != sha:
+    m = hashlib.sha256()
+    for f in rec.get("source_files", []):
+        try:
+            m.update(open(os.path.join(ROOT, f), "rb").read())
+        except OSError:
+            return None
+    if rec.get("source_sha256") != m.hexdigest():
         return None
     return rec.get("bytes_per_launch_c2")
 
@@ -177,8 +184,6 @@ def time_ours(args, w, x32, v32):
     run = pic.Run(params, device="cuda")
     stream = run.stream
     run.init(x32, v32)
-    if not args.no_tune and not args.variant:
-        run.autotune(reps=3)
     launches = {"n": 0}
 
     def one_step(ev=None):
@@ -195,6 +200,11 @@ def time_ours(args, w, x32, v32):
 
     for _ in range(args.warmup):
         one_step()
+    if not args.no_tune and not args.variant:
+        # tune on the state after the warm-up (past a sort), then re-warm
+        run.autotune(reps=8)
+        for _ in range(3):
+            one_step()
     torch.cuda.synchronize()
     K = args.steps
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -242,8 +252,9 @@ def time_e2e(args, w, x32, v32):
                         blocks_per_sm=args.bps, unroll=args.unroll)
     run = pic.Run(params, device="cuda")
     run.init(xh, vh)                      # warm: autotune, graph capture, first touch
+    run.step_n(w["sort_interval"] + 1)
     if not args.no_tune and not args.variant:
-        run.autotune(reps=3)
+        run.autotune(reps=8)
     run.step_n(w["sort_interval"] + 1)
     run.sync()
     torch.cuda.synchronize()
@@ -282,8 +293,8 @@ def tune_pool(states, steps, history):
     sample = [states[i] for i in order[:: max(1, len(order) // 48)]]
     nbytes = sum(pic.pool_run_bytes(p, history) for p, _, _ in sample) + (64 << 20)
     table = []
-    for variant in (1, 2, 5):
-        for cluster in (2, 4, 8):
+    for variant in (1, 2, 5, 1 + 16, 2 + 16, 5 + 16):
+        for cluster in (4, 8):
             for block in (256, 512):
                 try:
                     pool = pic.Pool(max_slots=len(sample), ncell_max=2048, arena_bytes=nbytes,
@@ -315,7 +326,10 @@ def time_batched(args):
     K, H = args.batched_steps, 16
     states = ensemble_states(args.batched_runs, 3)
     total_particles = sum(p.npart for p, _, _ in states)
-    best, table = tune_pool(states, 20, H)
+    if args.no_tune_batched:
+        best, table = (5 + 16, 8, 512), []
+    else:
+        best, table = tune_pool(states, 20, H)
     nbytes = sum(pic.pool_run_bytes(p, H) for p, _, _ in states) + (64 << 20)
     pool = pic.Pool(max_slots=len(states), ncell_max=2048, arena_bytes=nbytes, history=H,
                     variant=best[0], cluster=best[1], block=best[2])
@@ -349,6 +363,7 @@ def time_batched(args):
     t_plain = e0.elapsed_time(e1) / 1e3
     for r in runs:
         r.close()
+    args.pool_variant = best[0]          # reused by the served section
     return {"runs": len(states), "steps": K, "particles": total_particles,
             "value": total_particles * K / t_batched, "unit": "particle-steps/s",
             "seconds": t_batched, "plain_value": total_particles * K / t_plain,
@@ -420,8 +435,9 @@ def time_served(args):
     reqs = serve.requests_from_stream(stream,
                                       modes_fn=lambda r: W.two_stream_modes_1_to_8(1e-4, r["seed"]))
     budget = 150 * (1 << 30)
+    variant = getattr(args, "pool_variant", 5)
     srv = serve.Server(arena_bytes=budget, max_slots=2048, ncell_max=4096, history=8,
-                       advance_steps=args.serve_advance, variant=2, cluster=8, block=256)
+                       advance_steps=args.serve_advance, variant=variant, cluster=8, block=512)
     _, stats = srv.serve(reqs)
     srv.close()
     stats.update({"unit": "particle-steps/s", "budget_bytes": budget,
@@ -484,6 +500,9 @@ def main():
     if ws > 1:
         torch.distributed.init_process_group("nccl")
     torch.cuda.set_device(local)
+    if args.only_batched:
+        print(json.dumps({"batched": time_batched(args)}))
+        return
     x32, v32 = make_state(w)
     res = time_ours(args, w, x32, v32)
     e2e = None if args.no_e2e else time_e2e(args, w, x32, v32)
@@ -527,7 +546,9 @@ def main():
                      "frac": achieved / peak, "traffic": recorded_traffic(),
                      "kernel": "pic_push_fixed_kernel", "peak_source": src,
                      "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP,
-                     "push_ms_avg": push_avg_s * 1e3},
+                     "push_ms_avg": push_avg_s * 1e3,
+                     "push_ms_by_window": [round(statistics.mean(res["push_ms"][i:i + 100]), 4)
+                                           for i in range(0, len(res["push_ms"]), 100)]},
         "gpu_launches": res["launches"],
         "clocks": res["clocks"],
     }

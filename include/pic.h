@@ -248,16 +248,23 @@ int pic_load_two_stream(const pic_loading *ld, int64_t n, double length, void *x
 /* pic_init with the state generated on the device by pic_load_two_stream. */
 int pic_init_loaded(pic_run *run, const pic_loading *ld);
 
+/* Set the launch shape of the fused push (deposit variant, block size, unroll,
+ * resident blocks per SM; 0 keeps the current value / picks the default).
+ * Drops the captured graphs.  PIC_EINVAL for a shape the kernel cannot run. */
+int pic_set_launch(pic_run *run, int32_t variant, int32_t block, int32_t unroll,
+                   int32_t blocks_per_sm);
+
 /* One timed candidate of pic_autotune. */
 typedef struct pic_tune_entry {
     int32_t variant, block, unroll, grid;
-    float ms;                 /* median CUDA-event time of one fused push     */
+    float ms;                 /* mean CUDA-event time of one fused push      */
 } pic_tune_entry;
 
 /* Autotune the fused push (PIC_FP32_FIXED): time every candidate shape
  * (deposit variant x block size x unroll) for `reps` pushes on a copy of the
  * current particles (the sort buffers and a scratch density accumulator; the
- * run's state is untouched), then adopt the fastest.  Writes up to
+ * run's state is untouched) and, when the run sorts, on a freshly sorted copy
+ * too; adopt the one with the smallest mean time.  Writes up to
  * max_results entries to results (may be NULL) and their count to *nresults.
  * Synchronises.  PIC_ESTATE before pic_init or between pic_push and
  * pic_solve_field. */
@@ -282,9 +289,12 @@ typedef struct pic_pool_config {
     int32_t max_slots;     /* runs held at once (>= 1)                         */
     int32_t ncell_max;     /* largest NG admitted (<= PIC_NCELL_MAX)            */
     int32_t history;       /* diagnostics rows kept per run (>= 1)              */
-    int32_t variant;       /* PIC_DEPOSIT_ATOMIC | _MATCH | _QUAD (0 = MATCH)  */
+    int32_t variant;       /* PIC_DEPOSIT_ATOMIC | _MATCH | _QUAD (0 = MATCH);
+                              + 16: kernel built for two blocks per SM
+                              (64 registers) instead of one                  */
     int32_t cluster;       /* blocks per cluster: 1, 2, 4, 8 (0 = 8)            */
-    int32_t block;         /* threads per block: 128 .. 512 (0 = 256)           */
+    int32_t block;         /* threads per block: 128 .. 512 (0 = 256); the
+                              shape needs ceil(ncell_max / cluster) <= block   */
 } pic_pool_config;
 
 /* Arena bytes one run with parameters *p takes in a pool with `history`

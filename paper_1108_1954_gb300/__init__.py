@@ -92,6 +92,7 @@ _SIG = {
     "pic_launch_shape": (C.c_int, [_VP, C.POINTER(C.c_int32),
                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "pic_autotune": (C.c_int, [_VP, C.c_int32, _VP, C.c_int32, C.POINTER(C.c_int32)]),
+    "pic_set_launch": (C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     "pic_load_two_stream": (C.c_int, [_VP, C.c_int64, C.c_double, _VP, _VP, _VP]),
     "pic_init_loaded": (C.c_int, [_VP, _VP]),
     "pic_pool_admit_loaded": (C.c_int, [_VP, _P, _VP, C.c_int64, C.POINTER(C.c_int32)]),
@@ -290,6 +291,11 @@ class Run:
             return self.workspace[off:off + count * size].view(dt)
         return (view(x.value, n, tdt, es), view(v.value, n, tdt, es),
                 view(e.value, self.p.ncell, torch.float32, 4))
+
+    def set_launch(self, variant: int = 0, block: int = 0, unroll: int = 0,
+                   blocks_per_sm: int = 0):
+        _check(_lib.pic_set_launch(self._h, int(variant), int(block), int(unroll),
+                                   int(blocks_per_sm)), "pic_set_launch")
 
     def autotune(self, reps: int = 5) -> np.ndarray:
         """Time the candidate push shapes on a copy of the state and adopt

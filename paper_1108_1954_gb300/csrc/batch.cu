@@ -22,6 +22,9 @@
 //      block 0 reduces the slice diagnostics in rank order and writes the
 //      history rows.
 //
+// A slice has at most one node per thread (ceil(NG/C) <= block, checked by
+// the pool), so the integer solve of a slice is one block-wide scan.
+//
 // Every shared word a block reads from a peer was written before a cluster
 // barrier that the reader has passed, and is next overwritten (or its block
 // exits) only after a later barrier the reader must also reach, so three
@@ -38,7 +41,7 @@ namespace cg = cooperative_groups;
 namespace pic {
 namespace {
 
-constexpr int kMaxNodesPerThread = 2;   // ceil(ceil(NG/C)/block) <= 2 (host-checked)
+constexpr int kU = 2;                   // float4 groups per thread per iteration
 
 // The part of a block's shared memory its peers read.
 struct Exchange {
@@ -72,8 +75,6 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
 
     const int P = (ng + C - 1) / C;
     const int b0 = min(ng, r * P), b1 = min(ng, b0 + P);
-    const int kpt = (P + bs - 1) / bs;            // <= kMaxNodesPerThread
-    const int g0 = b0 + tid * kpt;                // this thread's first node
     const long long n4 = R.n >> 2;
     const long long qlo = n4 * r / C, qhi = n4 * (r + 1) / C;
     float4 *x4 = reinterpret_cast<float4 *>(R.x);
@@ -82,23 +83,45 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
 
     for (int s = 0; s < steps; s++) {
         const bool last = s == steps - 1;
-        // ---- A: push + deposit into the own tile
+        // ---- A: push + deposit into the own tile; kU float4 groups per
+        // thread per iteration, the next iteration's loads issued first
         float ke = 0.0f, mom = 0.0f;
-        for (long long q0 = qlo; q0 < qhi; q0 += bs) {
-            const long long q = q0 + tid;
-            const bool valid = q < qhi;
-            float4 xx = valid ? __ldcg(x4 + q) : zero4;
-            float4 vv = (push && valid) ? __ldcg(v4 + q) : zero4;
-            if (push && valid) {
-                push_particle(xx.x, vv.x, sE, c, ke, mom);
-                push_particle(xx.y, vv.y, sE, c, ke, mom);
-                push_particle(xx.z, vv.z, sE, c, ke, mom);
-                push_particle(xx.w, vv.w, sE, c, ke, mom);
+        {
+            const long long span = (long long)bs * kU;
+            float4 cx[kU], cv[kU];
+#pragma unroll
+            for (int u = 0; u < kU; u++) {
+                const long long q = qlo + u * bs + tid;
+                cx[u] = q < qhi ? __ldcg(x4 + q) : zero4;
+                cv[u] = (push && q < qhi) ? __ldcg(v4 + q) : zero4;
             }
-            deposit4<VARIANT>(tile, xx, valid, c, a.err, lane);
-            if (push && valid) {
-                __stcg(x4 + q, xx);
-                __stcg(v4 + q, vv);
+            for (long long q0 = qlo; q0 < qhi; q0 += span) {
+                float4 nx[kU], nv[kU];
+#pragma unroll
+                for (int u = 0; u < kU; u++) {
+                    const long long q = q0 + span + u * bs + tid;
+                    nx[u] = q < qhi ? __ldcg(x4 + q) : zero4;
+                    nv[u] = (push && q < qhi) ? __ldcg(v4 + q) : zero4;
+                }
+#pragma unroll
+                for (int u = 0; u < kU; u++) {
+                    const long long q = q0 + u * bs + tid;
+                    const bool valid = q < qhi;
+                    float4 xx = cx[u], vv = cv[u];
+                    if (push && valid) {
+                        push_particle(xx.x, vv.x, sE, c, ke, mom);
+                        push_particle(xx.y, vv.y, sE, c, ke, mom);
+                        push_particle(xx.z, vv.z, sE, c, ke, mom);
+                        push_particle(xx.w, vv.w, sE, c, ke, mom);
+                    }
+                    deposit4<VARIANT>(tile, xx, valid, c, a.err, lane);
+                    if (push && valid) {
+                        __stcg(x4 + q, xx);
+                        __stcg(v4 + q, vv);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kU; u++) { cx[u] = nx[u]; cv[u] = nv[u]; }
             }
         }
         if (r == 0 && tid < 32) {                 // the last N mod 4 particles
@@ -117,43 +140,30 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
         cl.sync();                                                    // #1
 
         // ---- B: node slice sums over the cluster's tiles
-        if (r == 0 && tid == 0) {
-            double k0 = 0.0, k1 = 0.0;
+        if (r == 0 && tid < 2) {
+            double k = 0.0;
+            for (int b = 0; b < C; b++) k += cl.map_shared_rank(&ex, b)->kv[tid];
+            kvtot[tid] = k;
+        }
+        // one node per thread: g = b0 + tid (the pool keeps ceil(NG/C) <= block)
+        const int g = b0 + tid;
+        const bool mine = g < b1;
+        unsigned long long rq = 0;
+        if (mine) {
             for (int b = 0; b < C; b++) {
-                const Exchange *pe = cl.map_shared_rank(&ex, b);
-                k0 += pe->kv[0];
-                k1 += pe->kv[1];
+                const unsigned *plo = cl.map_shared_rank(tile.lo, b);
+                const unsigned *phi = cl.map_shared_rank(tile.hi, b);
+                rq += ((unsigned long long)phi[g + 1] << 32) | plo[g + 1];
+                if (g == ng - 1) rq += ((unsigned long long)phi[0] << 32) | plo[0];
+                if (g == 0) rq += ((unsigned long long)phi[ng + 1] << 32) | plo[ng + 1];
             }
-            kvtot[0] = k0;
-            kvtot[1] = k1;
         }
-        i128 Rg[kMaxNodesPerThread];
-        unsigned long long rq[kMaxNodesPerThread];
-        i128 S0 = 0, S1 = 0, Sz = 0;
-        unsigned long long cq = 0;
-#pragma unroll
-        for (int i = 0; i < kMaxNodesPerThread; i++) {
-            const int g = g0 + i;
-            unsigned long long q = 0;
-            if (i < kpt && g < b1) {
-                for (int b = 0; b < C; b++) {
-                    const unsigned *plo = cl.map_shared_rank(tile.lo, b);
-                    const unsigned *phi = cl.map_shared_rank(tile.hi, b);
-                    q += ((unsigned long long)phi[g + 1] << 32) | plo[g + 1];
-                    if (g == ng - 1) q += ((unsigned long long)phi[0] << 32) | plo[0];
-                    if (g == 0) q += ((unsigned long long)phi[ng + 1] << 32) | plo[ng + 1];
-                }
-                Rg[i] = (i128)ntot - (i128)ng * (i128)q;
-                S0 += Rg[i];
-                S1 += Rg[i] * (i128)g;
-            } else {
-                Rg[i] = 0;
-            }
-            rq[i] = q;
-            cq += q;
+        const i128 Rg = mine ? (i128)ntot - (i128)ng * (i128)rq : (i128)0;
+        {
+            i128 S0 = Rg, S1 = Rg * (i128)g, Sz = 0;
+            block_sum3_i128(S0, S1, Sz, sh128);
+            if (tid == 0) { ex.s0 = S0; ex.s1 = S1; }
         }
-        block_sum3_i128(S0, S1, Sz, sh128);
-        if (tid == 0) { ex.s0 = S0; ex.s1 = S1; }
         cl.sync();                                                    // #2
 
         // prefixes from the slice sums of all blocks, in rank order
@@ -167,56 +177,38 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
         }
         const i128 SP = (i128)ng * SR - SS1;          // sum_k (NG-k) R_k
         const i128 A1 = (i128)b0 * A0 - B;             // sum_{k<b0} (b0-k) R_k
-        // inclusive prefix of R over the slice -> P_g; exclusive prefix of P
-        i128 tsum = 0;
-#pragma unroll
-        for (int i = 0; i < kMaxNodesPerThread; i++) tsum += Rg[i];
-        i128 ttot;
-        const i128 texcl = block_inclusive_scan_i128(tsum, sh128, ttot) - tsum;
-        i128 Pg[kMaxNodesPerThread];
-        i128 run = A0 + texcl, psum = 0;
-#pragma unroll
-        for (int i = 0; i < kMaxNodesPerThread; i++) {
-            run += Rg[i];
-            Pg[i] = run;
-            if (i < kpt && g0 + i < b1) psum += run;
-        }
-        const i128 pexcl0 = block_inclusive_scan_i128(psum, sh128, ttot) - psum;
-        // M_{g0-1}: previous thread's last node, or the slice's left neighbour
-        const i128 Mlast = (i128)ng * Pg[kMaxNodesPerThread - 1] - SP;
-        i128 Mprev = shfl_up_i128(Mlast, 1);
+        i128 tot_;
+        const i128 Pg = A0 + block_inclusive_scan_i128(Rg, sh128, tot_);      // P_g
+        const i128 Pin = mine ? Pg : (i128)0;
+        const i128 pex = block_inclusive_scan_i128(Pin, sh128, tot_) - Pin;  // sum_{b0<=k<g} P_k
+        const i128 M = (i128)ng * Pg - SP;                                  // M_g
+        // M_{g-1}: previous thread, or the slice's left neighbour for tid 0
+        i128 Mprev = shfl_up_i128(M, 1);
         __shared__ i128 wlast[32];
-        if (lane == 31) wlast[tid >> 5] = Mlast;
+        if (lane == 31) wlast[tid >> 5] = M;
         __syncthreads();
         if (lane == 0)
             Mprev = tid == 0 ? (b0 == 0 ? (i128)ng * SR - SP : (i128)ng * A0 - SP)
                              : wlast[(tid >> 5) - 1];
         NodeDiag d;
         node_diag_reset(d);
-        i128 pex = pexcl0;
-#pragma unroll
-        for (int i = 0; i < kMaxNodesPerThread; i++) {
-            const int g = g0 + i;
-            if (i < kpt && g < b1) {
-                const i128 M = (i128)ng * Pg[i] - SP;
-                const double E = R.k_e * i128_to_f64(M + Mprev);
-                const float E32 = (float)E;
-                sE[g + 1] = E32;
-                if (g == ng - 1) sE[0] = E32;
-                if (g == 0) sE[ng + 1] = E32;
-                if (last) {
-                    const i128 sumM = (i128)ng * (A1 + pex) - (i128)g * SP;
-                    R.E64[g] = E;
-                    R.E32[g] = E32;
-                    R.phi[g] = R.k_phi * i128_to_f64(sumM);
-                    R.rho[g] = R.k_rho * i128_to_f64(Rg[i]);
-                    R.rho_q_last[g] = rq[i];
-                }
-                node_diag(d, g, ng, E, E32);
-                pex += Pg[i];
-                Mprev = M;
+        if (mine) {
+            const double E = R.k_e * i128_to_f64(M + Mprev);
+            const float E32 = (float)E;
+            sE[g + 1] = E32;
+            if (g == ng - 1) sE[0] = E32;
+            if (g == 0) sE[ng + 1] = E32;
+            if (last) {
+                const i128 sumM = (i128)ng * (A1 + pex) - (i128)g * SP;
+                R.E64[g] = E;
+                R.E32[g] = E32;
+                R.phi[g] = R.k_phi * i128_to_f64(sumM);
+                R.rho[g] = R.k_rho * i128_to_f64(Rg);
+                R.rho_q_last[g] = rq;
             }
+            node_diag(d, g, ng, E, E32);
         }
+        const unsigned long long cq = rq;
         {
             double dv[1] = {d.fe};
             block_sum_t<1, double>(dv, shd);
@@ -250,15 +242,23 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
             tile.lo[j] = 0u;
             tile.hi[j] = 0u;
         }
-        if (r == 0 && tid == 0) {
-            double tot[kDiagFields];
-            for (int f = 0; f < kDiagFields; f++) tot[f] = 0.0;
-            unsigned long long cqt = 0;
-            for (int b = 0; b < C; b++) {
-                const Exchange *pe = cl.map_shared_rank(&ex, b);
-                for (int f = 0; f < kDiagFields; f++) tot[f] += pe->diag[f];
-                cqt += pe->cq;
+        // block 0: field f of the diagnostics summed over the blocks by
+        // thread f (rank order), then one thread writes the history rows
+        __shared__ double tot[kDiagFields];
+        __shared__ unsigned long long cqt;
+        if (r == 0 && tid <= kDiagFields) {
+            if (tid < kDiagFields) {
+                double acc = 0.0;
+                for (int b = 0; b < C; b++) acc += cl.map_shared_rank(&ex, b)->diag[tid];
+                tot[tid] = acc;
+            } else {
+                unsigned long long acc = 0;
+                for (int b = 0; b < C; b++) acc += cl.map_shared_rank(&ex, b)->cq;
+                cqt = acc;
             }
+        }
+        __syncthreads();
+        if (r == 0 && tid == 0) {
             long long n = step0 + s;
             if (push) {
                 pic_diag_row *row = &R.hist[n % R.hist_len];
@@ -284,8 +284,10 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
     if (r == 0 && tid == 0 && push) *R.step = step0 + steps;
 }
 
-template <int VARIANT>
-__global__ void __launch_bounds__(512) pic_batch_kernel(BatchArgs a) {
+// MINB = 1: up to 128 registers, no spills; MINB = 2: 64 registers, two
+// 512-thread blocks per SM (twice the warps), spills in the per-step solve.
+template <int VARIANT, int MINB>
+__global__ void __launch_bounds__(512, MINB) pic_batch_kernel(BatchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Exchange ex;
     __shared__ i128 sh128[96];
@@ -316,13 +318,20 @@ __global__ void __launch_bounds__(512) pic_batch_kernel(BatchArgs a) {
 
 using BatchKernel = void (*)(BatchArgs);
 
-BatchKernel pick_batch(int variant) {
+template <int MINB>
+BatchKernel pick_batch_minb(int variant) {
     switch (variant) {
-        case PIC_DEPOSIT_ATOMIC: return &pic_batch_kernel<PIC_DEPOSIT_ATOMIC>;
-        case PIC_DEPOSIT_MATCH: return &pic_batch_kernel<PIC_DEPOSIT_MATCH>;
-        case PIC_DEPOSIT_QUAD: return &pic_batch_kernel<PIC_DEPOSIT_QUAD>;
+        case PIC_DEPOSIT_ATOMIC: return &pic_batch_kernel<PIC_DEPOSIT_ATOMIC, MINB>;
+        case PIC_DEPOSIT_MATCH: return &pic_batch_kernel<PIC_DEPOSIT_MATCH, MINB>;
+        case PIC_DEPOSIT_QUAD: return &pic_batch_kernel<PIC_DEPOSIT_QUAD, MINB>;
         default: return nullptr;
     }
+}
+
+// variant + 16 * (minb - 1) selects the instantiation
+BatchKernel pick_batch(int code) {
+    const int variant = code & 15, minb = code >> 4 ? 2 : 1;
+    return minb == 2 ? pick_batch_minb<2>(variant) : pick_batch_minb<1>(variant);
 }
 
 }  // namespace
@@ -336,11 +345,12 @@ size_t batch_smem_bytes(int ng_max, int cluster, int block) {
 cudaError_t batch_prepare_attributes() {
     const int bytes = (int)batch_smem_bytes(PIC_NCELL_MAX, 8, 512);
     const int vs[3] = {PIC_DEPOSIT_ATOMIC, PIC_DEPOSIT_MATCH, PIC_DEPOSIT_QUAD};
-    for (int v : vs) {
-        cudaError_t e = cudaFuncSetAttribute(pick_batch(v),
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        if (e != cudaSuccess) return e;
-    }
+    for (int v : vs)
+        for (int m = 0; m < 2; m++) {
+            cudaError_t e = cudaFuncSetAttribute(pick_batch(v + 16 * m),
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+            if (e != cudaSuccess) return e;
+        }
     return cudaSuccess;
 }
 

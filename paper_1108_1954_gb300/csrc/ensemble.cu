@@ -68,13 +68,16 @@ int check_cfg(const pic_pool_config *c) {
     return PIC_OK;
 }
 
-int check_shape(int variant, int cluster, int block, int ncell_max) {
+// variant + 16 (two blocks per SM, 64 registers) is accepted too.
+int check_shape(int code, int cluster, int block, int ncell_max) {
+    const int variant = code & 15;
+    if (code >> 4 > 1) return PIC_EINVAL;
     if (variant != PIC_DEPOSIT_ATOMIC && variant != PIC_DEPOSIT_MATCH && variant != PIC_DEPOSIT_QUAD)
         return PIC_EINVAL;
     if (cluster != 1 && cluster != 2 && cluster != 4 && cluster != 8) return PIC_EINVAL;
     if (block < 128 || block > 512 || block % 32) return PIC_EINVAL;
     const int P = (ncell_max + cluster - 1) / cluster;
-    if ((P + block - 1) / block > 2) return PIC_EINVAL;   // slice nodes per thread
+    if (P > block) return PIC_EINVAL;   // one slice node per thread
     return PIC_OK;
 }
 

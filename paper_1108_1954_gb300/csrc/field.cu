@@ -140,12 +140,28 @@ __global__ void __launch_bounds__(256) pic_solve_fixed_kernel(SolveArgs a) {
     //   A0 = sum_{k<b0} R_k, A1 = sum_{k<b0} (b0-k) R_k   (prefixes to b0)
     //   SP = sum_k (NG-k) R_k = sum_g P_g,  also sum_k R_k (= P_{NG-1}).
     i128 A0 = 0, A1 = 0, SP = 0, SR = 0;
-#pragma unroll 8
-    for (int k = t; k < ng; k += T) {
-        const i128 R = (i128)ntot - (i128)ng * (i128)__ldcg(&a.rho_q[k]);
-        SP += R * (i128)(ng - k);
-        SR += R;
-        if (k < b0) { A0 += R; A1 += R * (i128)(b0 - k); }
+    {
+        constexpr int kBatch = 8;   // loads in flight per thread
+        for (int k0 = t; k0 < ng; k0 += kBatch * T) {
+            unsigned long long q[kBatch];
+#pragma unroll
+            for (int i = 0; i < kBatch; i++) {
+                const int k = k0 + i * T;
+                q[i] = k < ng ? __ldcg(&a.rho_q[k]) : 0ull;
+            }
+#pragma unroll
+            for (int i = 0; i < kBatch; i++) {
+                const int k = k0 + i * T;
+                if (k < ng) {
+                    const i128 R = (i128)ntot - (i128)ng * (i128)q[i];
+                    SP += R * (long long)(ng - k);
+                    SR += R;
+                    const bool before = k < b0;
+                    A0 += before ? R : (i128)0;
+                    A1 += before ? R * (long long)(b0 - k) : (i128)0;
+                }
+            }
+        }
     }
     block_sum3_i128(A0, A1, SP, sh);
     {

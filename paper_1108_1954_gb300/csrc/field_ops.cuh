@@ -102,15 +102,22 @@ __device__ __forceinline__ void node_diag_reset(NodeDiag &d) {
     for (int m = 0; m < PIC_NMODES; m++) { d.re[m] = 0.f; d.im[m] = 0.f; }
 }
 
+// The mode sums of node g: E32 e^{-i m theta}, theta = 2 pi g / NG, for
+// m = 1..8, by one sincospi and the rotation e^{-i m theta} =
+// e^{-i (m-1) theta} e^{-i theta} (float32; a diagnostic).
 __device__ __forceinline__ void node_diag(NodeDiag &d, int g, int ng, double E, float E32) {
     d.fe = fma(E, E, d.fe);
+    float s1, c1;
+    sincospif(2.0f * (float)g / (float)ng, &s1, &c1);
+    float cm = c1, sm = s1;            // cos(m theta), sin(m theta)
 #pragma unroll
-    for (int m = 1; m <= PIC_NMODES; m++) {
-        const int ph = (int)(((long long)m * g) % ng);
-        float sn, cs;
-        sincospif(2.0f * (float)ph / (float)ng, &sn, &cs);
-        d.re[m - 1] = fmaf(E32, cs, d.re[m - 1]);
-        d.im[m - 1] = fmaf(-E32, sn, d.im[m - 1]);
+    for (int m = 0; m < PIC_NMODES; m++) {
+        d.re[m] = fmaf(E32, cm, d.re[m]);
+        d.im[m] = fmaf(-E32, sm, d.im[m]);
+        const float cn = cm * c1 - sm * s1;
+        const float sn = sm * c1 + cm * s1;
+        cm = cn;
+        sm = sn;
     }
 }
 

@@ -263,6 +263,16 @@ cudaError_t enqueue_sort(pic_run *r, cudaStream_t s) {
     return e;
 }
 
+// Sort buffer `from` into buffer 1-from (the run's current buffer is left as
+// it is).
+cudaError_t enqueue_sort_into(pic_run *r, int from, cudaStream_t s) {
+    const int saved = r->cur;
+    r->cur = from;
+    cudaError_t e = enqueue_sort(r, s);
+    r->cur = saved;
+    return e;
+}
+
 // One step on stream s: [sort] + push + solve.
 cudaError_t enqueue_step(pic_run *r, cudaStream_t s, bool sort) {
     cudaError_t e;
@@ -426,9 +436,9 @@ int pic_create(const pic_params *p, void *workspace, size_t workspace_bytes,
     r->k_phi = -r->dx * r->dx * r->k_rho / (double)p->ncell;
 
     // launch shape of the fused push
-    r->variant = p->deposit_variant ? p->deposit_variant : PIC_DEPOSIT_ATOMIC;
+    r->variant = p->deposit_variant ? p->deposit_variant : PIC_DEPOSIT_QUAD;
     if (p->precision != PIC_FP32_FIXED) r->variant = PIC_DEPOSIT_ATOMIC;
-    r->block = p->block_size ? p->block_size : 256;
+    r->block = p->block_size ? p->block_size : (p->precision == PIC_FP32_FIXED ? 512 : 256);
     r->unroll = p->unroll ? p->unroll : 1;
     if (p->precision != PIC_FP32_FIXED) r->unroll = 1;
     r->grid = push_grid(r, r->variant, r->block, r->unroll, p->blocks_per_sm);
@@ -607,6 +617,29 @@ int pic_launch_shape(const pic_run *run, int32_t *grid, int32_t *block, int32_t 
     return PIC_OK;
 }
 
+int pic_set_launch(pic_run *run, int32_t variant, int32_t block, int32_t unroll,
+                   int32_t blocks_per_sm) {
+    if (!run) return PIC_EINVAL;
+    if (run->pending_push) return PIC_ESTATE;
+    const bool fixed = run->p.precision == PIC_FP32_FIXED;
+    const int v = variant ? variant : run->variant;
+    const int b = block ? block : run->block;
+    const int u = unroll ? unroll : run->unroll;
+    if (v < PIC_DEPOSIT_ATOMIC || v > PIC_DEPOSIT_QUAD || (!fixed && v != PIC_DEPOSIT_ATOMIC))
+        return PIC_EINVAL;
+    if (b < 32 || b % 32 || b > (fixed ? 512 : 1024)) return PIC_EINVAL;
+    if ((u != 1 && u != 2 && u != 4) || (!fixed && u != 1)) return PIC_EINVAL;
+    if (blocks_per_sm < 0 || blocks_per_sm > 32) return PIC_EINVAL;
+    const int g = push_grid(run, v, b, u, blocks_per_sm);
+    if (g < 1) return PIC_EINVAL;
+    run->variant = v;
+    run->block = b;
+    run->unroll = u;
+    run->grid = g;
+    destroy_graphs(run);
+    return PIC_OK;
+}
+
 int pic_autotune(pic_run *run, int32_t reps, pic_tune_entry *results,
                  int32_t max_results, int32_t *nresults) {
     if (!run || reps < 1) return PIC_EINVAL;
@@ -625,6 +658,11 @@ int pic_autotune(pic_run *run, int32_t reps, pic_tune_entry *results,
     float best = 1e30f;
     int bv = run->variant, bb = run->block, bu = run->unroll, bg = run->grid, count = 0;
     int rc = PIC_OK;
+    // With sorting on, the particle order cycles between freshly sorted (many
+    // lanes of a warp in one cell) and drifted apart; each candidate is timed
+    // on a copy of the current order and on a freshly sorted copy, and the sum
+    // is minimised.
+    const int phases = run->p.sort_interval > 0 ? 2 : 1;
     for (int v : variants)
         for (int b : blocks)
             for (int u : unrolls) {
@@ -639,25 +677,34 @@ int pic_autotune(pic_run *run, int32_t reps, pic_tune_entry *results,
                 a.partials = run->at<double>(run->lay.partials);
                 a.err = &run->dev()->err;
                 a.c = run->pc;
-                cudaError_t e = cudaMemcpyAsync(a.x, run->xs(c), bytes, cudaMemcpyDeviceToDevice, run->stream);
-                if (e == cudaSuccess) e = cudaMemcpyAsync(a.v, run->vs(c), bytes, cudaMemcpyDeviceToDevice, run->stream);
-                if (e == cudaSuccess) e = launch_push_fixed(a, g, b, v, u, true, run->stream);  // warm
-                float times[64];
-                const int nrep = reps < 64 ? reps : 64;
-                for (int i = 0; i < nrep && e == cudaSuccess; i++) {
-                    e = cudaEventRecord(e0, run->stream);
-                    if (e == cudaSuccess) e = launch_push_fixed(a, g, b, v, u, true, run->stream);
-                    if (e == cudaSuccess) e = cudaEventRecord(e1, run->stream);
-                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-                    if (e == cudaSuccess) e = cudaEventElapsedTime(&times[i], e0, e1);
-                }
-                if (e != cudaSuccess) { rc = cuda_fail(e); goto done; }
-                // median
-                for (int i = 1; i < nrep; i++)
-                    for (int k = i; k > 0 && times[k] < times[k - 1]; k--) {
-                        float t = times[k]; times[k] = times[k - 1]; times[k - 1] = t;
+                float total = 0.0f;
+                for (int ph = 0; ph < phases; ph++) {
+                    cudaError_t e;
+                    if (ph == 0) {
+                        e = cudaMemcpyAsync(a.x, run->xs(c), bytes, cudaMemcpyDeviceToDevice, run->stream);
+                        if (e == cudaSuccess)
+                            e = cudaMemcpyAsync(a.v, run->vs(c), bytes, cudaMemcpyDeviceToDevice, run->stream);
+                    } else {
+                        e = enqueue_sort_into(run, c, run->stream);
                     }
-                const float med = times[nrep / 2];
+                    if (e == cudaSuccess) e = launch_push_fixed(a, g, b, v, u, true, run->stream);  // warm
+                    float times[64];
+                    const int nrep = reps < 64 ? reps : 64;
+                    for (int i = 0; i < nrep && e == cudaSuccess; i++) {
+                        e = cudaEventRecord(e0, run->stream);
+                        if (e == cudaSuccess) e = launch_push_fixed(a, g, b, v, u, true, run->stream);
+                        if (e == cudaSuccess) e = cudaEventRecord(e1, run->stream);
+                        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                        if (e == cudaSuccess) e = cudaEventElapsedTime(&times[i], e0, e1);
+                    }
+                    if (e != cudaSuccess) { rc = cuda_fail(e); goto done; }
+                    // the repeats push the copy onward (its order drifts),
+                    // so their mean is the figure of merit
+                    float sum = 0.0f;
+                    for (int i = 0; i < nrep; i++) sum += times[i];
+                    total += sum / (float)nrep;
+                }
+                const float med = total / (float)phases;
                 if (results && count < max_results) results[count] = pic_tune_entry{v, b, u, g, med};
                 count++;
                 if (med < best) { best = med; bv = v; bb = b; bu = u; bg = g; }

@@ -67,8 +67,8 @@ def requests_from_stream(stream, modes_fn=None):
 
 class Server:
     def __init__(self, arena_bytes: int, max_slots: int = 1024, ncell_max: int = 4096,
-                 history: int = 8, advance_steps: int = 50, variant: int = 2,
-                 cluster: int = 8, block: int = 256, device=None):
+                 history: int = 8, advance_steps: int = 50, variant: int = 5,
+                 cluster: int = 8, block: int = 512, device=None):
         self.pool = Pool(max_slots=max_slots, ncell_max=ncell_max, arena_bytes=arena_bytes,
                          history=history, variant=variant, cluster=cluster, block=block,
                          device=device)

@@ -75,8 +75,9 @@ def assert_same(pool, slot, ref, steps):
 
 
 @pytest.mark.parametrize("variant,cluster,block,ncell_max",
-                         [(2, 8, 256, 2048), (1, 8, 256, 2048), (5, 4, 256, 2048),
-                          (2, 2, 512, 2048), (2, 1, 512, 1024), (1, 4, 128, 1024)])
+                         [(2, 8, 256, 2048), (1, 8, 256, 2048), (5, 4, 512, 2048),
+                          (2, 2, 512, 1024), (2, 1, 512, 512), (1, 4, 256, 1024),
+                          (2 + 16, 8, 512, 4096), (5 + 16, 8, 256, 2048)])
 def test_batched_equals_alone(variant, cluster, block, ncell_max):
     runs = [r for r in run_set() if r[0].ncell <= ncell_max]
     steps = 23
@@ -163,3 +164,5 @@ def test_pool_rejects_bad_input():
         pool.configure(2, 3, 256)                            # cluster of 3
     with pytest.raises(pic.PicError):
         pool.configure(3, 8, 256)                            # packed variant
+    with pytest.raises(pic.PicError):
+        pool.configure(2, 1, 32)                             # 64 nodes > 32 threads
