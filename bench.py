@@ -66,9 +66,15 @@ def parse():
     ap.add_argument("--batched-runs", type=int, default=512)
     ap.add_argument("--batched-steps", type=int, default=500)
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-c1", action="store_true")
     ap.add_argument("--only-batched", action="store_true",
                     help="run only the batched-ensemble section (profiling)")
     ap.add_argument("--no-tune-batched", action="store_true")
+    ap.add_argument("--only-precision", action="store_true",
+                    help="run only the precision study (config 4)")
+    ap.add_argument("--only-variant-scan", action="store_true",
+                    help="mean push time of each deposit variant over two sort periods, "
+                         "at several points of the config-2 run")
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-advance", type=int, default=50)
     ap.add_argument("--precision", action="store_true",
@@ -76,6 +82,20 @@ def parse():
     ap.add_argument("--precision-steps", type=int, default=2000)
     ap.add_argument("--precision-oracle-steps", type=int, default=150)
     return ap.parse_args()
+
+
+def rank_aggregate(local_seconds, npart, steps, world_size, device="cpu"):
+    """Whole-job throughput over ranks that each advanced their own run of
+    `npart` particles by `steps`: the slowest rank's time (max over ranks)
+    and world_size * npart * steps / that time.  No collective on the data
+    path; this is the only cross-rank step."""
+    total_s = float(local_seconds)
+    if world_size > 1:
+        import torch
+        t = torch.tensor([total_s], device=device, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    return world_size * npart * steps / total_s, total_s
 
 
 def workload(name):
@@ -189,7 +209,7 @@ def time_ours(args, w, x32, v32):
     def one_step(ev=None):
         if S > 0 and run.step > 0 and run.step % S == 0:
             run.sort()
-            launches["n"] += 4
+            launches["n"] += 5
         if ev is not None:
             ev[0].record(stream)
         run.push()
@@ -425,6 +445,87 @@ def precision_study(args):
     return out
 
 
+def variant_scan(args):
+    """Mean fused-push time per (variant, block, unroll) over two whole sort
+    periods, restarting from the same state, at steps 0, 200 and 600 of the
+    config-2 run."""
+    import numpy as np
+    import torch
+    import paper_1108_1954_gb300 as pic
+    w = workload(args.workload)
+    x32, v32 = make_state(w)
+    S = w["sort_interval"]
+    run = pic.Run(pic.Params(npart=w["npart"], ncell=w["ncell"], length=w["length"],
+                             dt=w["dt"], sort_interval=S))
+    run.init(x32, v32)
+    stream = run.stream
+    out = []
+    for checkpoint in (0, 200, 600):
+        while run.step < checkpoint:
+            run.step_n(min(100, checkpoint - run.step))
+        xs, vs = run.get_state()
+        st = run.step
+        row = {"step": st}
+        for var in (1, 2, 5):
+            for blk, un in ((512, 1), (512, 2), (256, 1)):
+                run.set_state(xs, vs, st)
+                run.set_launch(var, blk, un)
+                ev = [(torch.cuda.Event(True), torch.cuda.Event(True)) for _ in range(2 * S)]
+                for a, b in ev:
+                    if run.step > 0 and run.step % S == 0:
+                        run.sort()
+                    a.record(stream)
+                    run.push()
+                    b.record(stream)
+                    run.solve_field()
+                torch.cuda.synchronize()
+                row["%d/%d/%d" % (var, blk, un)] = round(float(np.mean(
+                    [a.elapsed_time(b) for a, b in ev])), 4)
+        run.set_state(xs, vs, st)
+        out.append(row)
+    run.close()
+    return out
+
+
+def time_c1(args):
+    """Config 1 (20,000 electrons, 64 cells, 200 steps): launch-bound, so
+    reported as microseconds per step -- through pic_step_n (CUDA graphs of
+    16 steps) and as a one-run pool (all 200 steps in one cluster launch)."""
+    import torch
+    import workloads as W
+    import paper_1108_1954_gb300 as pic
+    n, ng, L, K = 20000, 64, 4.0 * math.pi, 200
+    x, v = W.two_stream(n, L, 0.2, 0.01, 1)
+    x32, v32 = W.to_f32_state(x, v, L)
+    run = pic.Run(pic.Params(npart=n, ncell=ng, length=L, dt=0.1, history=K + 1))
+    run.init(x32, v32)
+    run.step_n(32)                    # capture the graph
+    run.init(x32, v32)
+    s = run.stream
+    e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+    e0.record(s)
+    run.step_n(K)
+    e1.record(s)
+    torch.cuda.synchronize()
+    t_graph = e0.elapsed_time(e1) / 1e3
+    run.close()
+    pool = pic.Pool(max_slots=1, ncell_max=64, arena_bytes=1 << 24, history=K + 1,
+                    variant=5, cluster=1, block=256)
+    slot = pool.admit(pic.Params(npart=n, ncell=ng, length=L, dt=0.1), x32, v32, K)
+    pool.advance(0)
+    pool.sync()
+    e0.record(pool.stream)
+    pool.advance(K)
+    e1.record(pool.stream)
+    pool.sync()
+    t_pool = e0.elapsed_time(e1) / 1e3
+    pool.close()
+    return {"npart": n, "ncell": ng, "steps": K,
+            "us_per_step_graphs": 1e6 * t_graph / K, "us_per_step_one_launch": 1e6 * t_pool / K,
+            "value_graphs": n * K / t_graph, "value_one_launch": n * K / t_pool,
+            "unit": "particle-steps/s"}
+
+
 def time_served(args):
     """Config 5: Poisson arrivals (mean 200/s) of run requests served by the
     continuous-batching loop within a 150 GB device-memory budget."""
@@ -503,20 +604,22 @@ def main():
     if args.only_batched:
         print(json.dumps({"batched": time_batched(args)}))
         return
+    if args.only_precision:
+        print(json.dumps({"precision": precision_study(args)}))
+        return
+    if args.only_variant_scan:
+        print(json.dumps({"variant_scan_push_ms": variant_scan(args)}))
+        return
     x32, v32 = make_state(w)
     res = time_ours(args, w, x32, v32)
     e2e = None if args.no_e2e else time_e2e(args, w, x32, v32)
+    c1 = None if args.no_c1 else time_c1(args)
     batched = None if args.no_batched else time_batched(args)
     served = None if args.no_served else time_served(args)
     precision = precision_study(args) if (args.precision and rank == 0) else None
 
     n, K = w["npart"], res["steps"]
-    total_s = res["total_ms"] / 1e3
-    if ws > 1:
-        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = ws * n * K / total_s
+    value, total_s = rank_aggregate(res["total_ms"] / 1e3, n, K, ws, device="cuda")
     push_avg_s = statistics.mean(res["push_ms"]) / 1e3
     achieved = BYTES_PER_PARTICLE_STEP * n / push_avg_s / 1e9
     peak, src = measured_peak()
@@ -558,6 +661,8 @@ def main():
                        "d2h_bytes_per_step": e2e["d2h_per_step"]}
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if c1 is not None:
+        line["c1"] = c1
     if batched is not None:
         line["batched"] = batched
     if served is not None:

@@ -213,6 +213,16 @@ int pic_set_state(pic_run *run, const void *x, const void *v, int64_t step);
 int pic_get_field(pic_run *run, double *rho, double *phi, double *E,
                   int64_t *rho_q);
 
+/* Phase-space histogram f(x, v) of the current particles (the (x, v)
+ * snapshots of the Sec. 4 two-stream test, Fig. 1): counts[iv * nx + ix] (host,
+ * nx * nv uint32) of the particles with ix = min(nx - 1, trunc(x * (nx/L))) and
+ * iv = floor((v - vmin) * (nv/(vmax - vmin))), both scale factors and the
+ * products in float32; particles with iv outside [0, nv) are not counted.
+ * nx * nv <= PIC_PHASE_MAX_BINS, vmax > vmin, else PIC_EINVAL.  Synchronises. */
+#define PIC_PHASE_MAX_BINS 16384
+int pic_phase_space(pic_run *run, int32_t nx, int32_t nv, double vmin, double vmax,
+                    uint32_t *counts);
+
 /* Device pointers of the current particle arrays (they alternate after each
  * sort) and of the float32 field used by the gather. */
 int pic_device_arrays(pic_run *run, void **x, void **v, void **E32);

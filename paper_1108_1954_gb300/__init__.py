@@ -93,6 +93,7 @@ _SIG = {
                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "pic_autotune": (C.c_int, [_VP, C.c_int32, _VP, C.c_int32, C.POINTER(C.c_int32)]),
     "pic_set_launch": (C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
+    "pic_phase_space": (C.c_int, [_VP, C.c_int32, C.c_int32, C.c_double, C.c_double, _VP]),
     "pic_load_two_stream": (C.c_int, [_VP, C.c_int64, C.c_double, _VP, _VP, _VP]),
     "pic_init_loaded": (C.c_int, [_VP, _VP]),
     "pic_pool_admit_loaded": (C.c_int, [_VP, _P, _VP, C.c_int64, C.POINTER(C.c_int32)]),
@@ -274,6 +275,13 @@ class Run:
         _check(_lib.pic_get_field(self._h, _VP(rho.ctypes.data), _VP(phi.ctypes.data),
                                   _VP(E.ctypes.data), _VP(rq.ctypes.data)), "pic_get_field")
         return dict(rho=rho, phi=phi, E=E, rho_q=rq)
+
+    def phase_space(self, nx: int, nv: int, vmin: float, vmax: float) -> np.ndarray:
+        """f(x, v) counts, shape (nv, nx): row iv, column ix."""
+        out = np.zeros((int(nv), int(nx)), dtype=np.uint32)
+        _check(_lib.pic_phase_space(self._h, int(nx), int(nv), float(vmin), float(vmax),
+                                    _VP(out.ctypes.data)), "pic_phase_space")
+        return out
 
     def device_arrays(self):
         """Torch views (x, v, E32) of the current device arrays."""

@@ -42,6 +42,7 @@ namespace pic {
 namespace {
 
 constexpr int kU = 2;                   // float4 groups per thread per iteration
+constexpr int kMaxCluster = 8;          // blocks per cluster (portable limit)
 
 // The part of a block's shared memory its peers read.
 struct Exchange {
@@ -141,8 +142,13 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
 
         // ---- B: node slice sums over the cluster's tiles
         if (r == 0 && tid < 2) {
+            double part[kMaxCluster];
+#pragma unroll
+            for (int b = 0; b < kMaxCluster; b++)
+                part[b] = b < C ? cl.map_shared_rank(&ex, b)->kv[tid] : 0.0;
             double k = 0.0;
-            for (int b = 0; b < C; b++) k += cl.map_shared_rank(&ex, b)->kv[tid];
+#pragma unroll
+            for (int b = 0; b < kMaxCluster; b++) k += part[b];
             kvtot[tid] = k;
         }
         // one node per thread: g = b0 + tid (the pool keeps ceil(NG/C) <= block)
@@ -166,14 +172,23 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
         }
         cl.sync();                                                    // #2
 
-        // prefixes from the slice sums of all blocks, in rank order
+        // prefixes from the slice sums of all blocks, in rank order (the
+        // C remote reads issued together)
         i128 A0 = 0, B = 0, SR = 0, SS1 = 0;
-        for (int b = 0; b < C; b++) {
-            const Exchange *pe = cl.map_shared_rank(&ex, b);
-            const i128 t0 = pe->s0, t1 = pe->s1;
-            if (b < r) { A0 += t0; B += t1; }
-            SR += t0;
-            SS1 += t1;
+        {
+            i128 t0[kMaxCluster], t1[kMaxCluster];
+#pragma unroll
+            for (int b = 0; b < kMaxCluster; b++) {
+                const Exchange *pe = cl.map_shared_rank(&ex, b < C ? b : 0);
+                t0[b] = b < C ? pe->s0 : (i128)0;
+                t1[b] = b < C ? pe->s1 : (i128)0;
+            }
+#pragma unroll
+            for (int b = 0; b < kMaxCluster; b++) {
+                if (b < r) { A0 += t0[b]; B += t1[b]; }
+                SR += t0[b];
+                SS1 += t1[b];
+            }
         }
         const i128 SP = (i128)ng * SR - SS1;          // sum_k (NG-k) R_k
         const i128 A1 = (i128)b0 * A0 - B;             // sum_{k<b0} (b0-k) R_k
@@ -248,12 +263,22 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
         __shared__ unsigned long long cqt;
         if (r == 0 && tid <= kDiagFields) {
             if (tid < kDiagFields) {
+                double part[kMaxCluster];
+#pragma unroll
+                for (int b = 0; b < kMaxCluster; b++)
+                    part[b] = b < C ? cl.map_shared_rank(&ex, b)->diag[tid] : 0.0;
                 double acc = 0.0;
-                for (int b = 0; b < C; b++) acc += cl.map_shared_rank(&ex, b)->diag[tid];
+#pragma unroll
+                for (int b = 0; b < kMaxCluster; b++) acc += part[b];
                 tot[tid] = acc;
             } else {
+                unsigned long long part[kMaxCluster];
+#pragma unroll
+                for (int b = 0; b < kMaxCluster; b++)
+                    part[b] = b < C ? cl.map_shared_rank(&ex, b)->cq : 0ull;
                 unsigned long long acc = 0;
-                for (int b = 0; b < C; b++) acc += cl.map_shared_rank(&ex, b)->cq;
+#pragma unroll
+                for (int b = 0; b < kMaxCluster; b++) acc += part[b];
                 cqt = acc;
             }
         }

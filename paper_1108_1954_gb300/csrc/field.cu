@@ -89,14 +89,24 @@ __device__ void finalize(const SolveArgs &a, long long step) {
         else if (a.mode == PIC_FP32_ATOMIC) a.rho_f32[g] = 0.0f;
         else a.rho_f64[g] = 0.0;
     }
+    // all the partials' loads in flight at once, summed in block order
     const int f = threadIdx.x;
+    const int nb = (int)gridDim.x;
     if (f < kDiagFields) {
+        double part[kSolveMaxBlocks];
+#pragma unroll
+        for (int b = 0; b < kSolveMaxBlocks; b++) part[b] = b < nb ? __ldcg(&a.dpart[b].v[f]) : 0.0;
         double acc = 0.0;
-        for (int b = 0; b < (int)gridDim.x; b++) acc += __ldcg(&a.dpart[b].v[f]);
+#pragma unroll
+        for (int b = 0; b < kSolveMaxBlocks; b++) acc += part[b];
         tot[f] = acc;
     } else if (f == kDiagFields) {
+        unsigned long long part[kSolveMaxBlocks];
+#pragma unroll
+        for (int b = 0; b < kSolveMaxBlocks; b++) part[b] = b < nb ? __ldcg(&a.dpart[b].cq) : 0ull;
         unsigned long long acc = 0;
-        for (int b = 0; b < (int)gridDim.x; b++) acc += __ldcg(&a.dpart[b].cq);
+#pragma unroll
+        for (int b = 0; b < kSolveMaxBlocks; b++) acc += part[b];
         tot_cq = acc;
     }
     __syncthreads();

@@ -70,7 +70,9 @@ static __device__ void block_sum3_i128(i128 &a, i128 &b, i128 &c, i128 *sh /*[96
     __syncthreads();
 }
 
-// Block sum of K doubles, fixed order; result valid in thread 0.
+// Block sum of K values per thread, fixed order; result valid in thread 0.
+// Warp sums by shuffles; the cross-warp sum of value i by lane i of warp 0
+// (all lanes in parallel), then gathered to thread 0.
 template <int K, typename T>
 static __device__ void block_sum_t(T (&v)[K], T *sh /*[32*K]*/) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -78,14 +80,17 @@ static __device__ void block_sum_t(T (&v)[K], T *sh /*[32*K]*/) {
     for (int i = 0; i < K; i++)
         for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(kFull, v[i], o);
     if (lane == 0)
+#pragma unroll
         for (int i = 0; i < K; i++) sh[w * K + i] = v[i];
     __syncthreads();
-    if (threadIdx.x == 0)
-        for (int i = 0; i < K; i++) {
-            T s = 0;
-            for (int j = 0; j < nw; j++) s += sh[j * K + i];
-            v[i] = s;
-        }
+    if (w == 0) {
+        static_assert(K <= 32, "one lane per value");
+        T s = 0;
+        if (lane < K)
+            for (int j = 0; j < nw; j++) s += sh[j * K + lane];
+#pragma unroll
+        for (int i = 0; i < K; i++) v[i] = __shfl_sync(kFull, s, i);
+    }
     __syncthreads();
 }
 

@@ -1,0 +1,54 @@
+// phase.cu -- phase-space histogram f(x, v) of the particles (the (x, v)
+// snapshots of the Sec. 4 verification test, Fig. 1), on the device.
+//
+// Bin rule (float32, as stated in include/pic.h): ix = min(nx - 1,
+// trunc(x * (nx / L))), iv = floor((v - vmin) * (nv / (vmax - vmin))); a
+// particle with iv outside [0, nv) is not counted.  Each block counts into a
+// shared-memory copy of the grid (32-bit atomics) and adds it to the global
+// counts once.
+#include "pic_internal.cuh"
+
+namespace pic {
+namespace {
+
+template <typename T>
+__global__ void __launch_bounds__(256) pic_phase_kernel(PhaseArgs<T> a) {
+    extern __shared__ unsigned sh[];
+    const int cells = a.nx * a.nv;
+    for (int i = threadIdx.x; i < cells; i += blockDim.x) sh[i] = 0u;
+    __syncthreads();
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += stride) {
+        const float x = (float)a.x[p], v = (float)a.v[p];
+        const float fx = x * a.sx;
+        const float fv = floorf((v - a.vmin) * a.sv);
+        if (!(fx >= 0.0f) || !(fv >= 0.0f) || !(fv < (float)a.nv)) continue;
+        int ix = (int)fx;
+        ix = ix < a.nx ? ix : a.nx - 1;
+        atomicAdd(&sh[(int)fv * a.nx + ix], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < cells; i += blockDim.x)
+        if (sh[i]) atomicAdd(&a.counts[i], sh[i]);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_phase(const PhaseArgs<T> &a, int sms, cudaStream_t s) {
+    long long blocks = (a.n + 255) / 256;
+    if (blocks > (long long)sms * 4) blocks = (long long)sms * 4;
+    if (blocks < 1) blocks = 1;
+    const size_t smem = (size_t)a.nx * a.nv * sizeof(unsigned);
+    cudaError_t e = cudaFuncSetAttribute(&pic_phase_kernel<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(kPhaseMaxBins * sizeof(unsigned)));
+    if (e != cudaSuccess) return e;
+    pic_phase_kernel<T><<<(unsigned)blocks, 256, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_phase<float>(const PhaseArgs<float> &, int, cudaStream_t);
+template cudaError_t launch_phase<double>(const PhaseArgs<double> &, int, cudaStream_t);
+
+}  // namespace pic

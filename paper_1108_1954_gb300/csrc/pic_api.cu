@@ -52,7 +52,7 @@ struct Layout {
     size_t x[2], v[2];
     size_t rho_q, rho_q_last, rho_f32, rho_f64;
     size_t rho, phi, E64, E32;
-    size_t partials, dpart, hist, dev, tune_rho;
+    size_t partials, dpart, hist, dev, tune_rho, phase;
     size_t s_hist, s_segtot, s_base;
     size_t total;
     int hist_len;
@@ -105,6 +105,7 @@ void make_layout(const pic_params *p, Layout *L) {
     L->hist = take((size_t)L->hist_len * sizeof(pic_diag_row));
     L->dev = take(sizeof(DevScalars));
     L->tune_rho = take(ng * 8);
+    L->phase = take((size_t)kPhaseMaxBins * 4);
     sort_geometry(p->npart, &L->nchunk, &L->chunk, &L->nseg, &L->seg_len);
     L->s_hist = take((size_t)L->nchunk * ng * 4);
     L->s_segtot = take((size_t)L->nseg * ng * 4);
@@ -597,6 +598,31 @@ int pic_get_field(pic_run *run, double *rho, double *phi, double *E, int64_t *rh
         else
             std::memset(rho_q, 0, ng * 8);
     }
+    PIC_CUDA(cudaStreamSynchronize(run->stream));
+    return read_error_word(run);
+}
+
+int pic_phase_space(pic_run *run, int32_t nx, int32_t nv, double vmin, double vmax,
+                    uint32_t *counts) {
+    if (!run || !counts || nx < 1 || nv < 1 || (long long)nx * nv > PIC_PHASE_MAX_BINS ||
+        !(vmax > vmin) || !std::isfinite(vmin) || !std::isfinite(vmax))
+        return PIC_EINVAL;
+    if (!run->ready) return PIC_ESTATE;
+    unsigned *d = run->at<unsigned>(run->lay.phase);
+    const size_t bytes = (size_t)nx * nv * 4;
+    PIC_CUDA(cudaMemsetAsync(d, 0, bytes, run->stream));
+    const float sx = (float)((double)nx / run->p.length);
+    const float sv = (float)((double)nv / (vmax - vmin));
+    if (run->p.precision == PIC_FP64) {
+        PhaseArgs<double> a{(const double *)run->xs(run->cur), (const double *)run->vs(run->cur),
+                            run->p.npart, nx, nv, sx, (float)vmin, sv, d};
+        PIC_CUDA(launch_phase(a, run->sms, run->stream));
+    } else {
+        PhaseArgs<float> a{(const float *)run->xs(run->cur), (const float *)run->vs(run->cur),
+                           run->p.npart, nx, nv, sx, (float)vmin, sv, d};
+        PIC_CUDA(launch_phase(a, run->sms, run->stream));
+    }
+    PIC_CUDA(cudaMemcpyAsync(counts, d, bytes, cudaMemcpyDeviceToHost, run->stream));
     PIC_CUDA(cudaStreamSynchronize(run->stream));
     return read_error_word(run);
 }

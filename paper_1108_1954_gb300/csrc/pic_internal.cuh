@@ -160,6 +160,20 @@ cudaError_t launch_load(const LoadArgs &a, int sms, cudaStream_t s);
 int make_load_args(const pic_loading *ld, long long n, double length, float *x, float *v,
                    LoadArgs *out);
 
+// Phase-space histogram (phase.cu).
+constexpr int kPhaseMaxBins = 16384;
+template <typename T>
+struct PhaseArgs {
+    const T *x, *v;
+    long long n;
+    int nx, nv;
+    float sx;             // nx / L
+    float vmin, sv;       // nv / (vmax - vmin)
+    unsigned *counts;     // [nv][nx]
+};
+template <typename T>
+cudaError_t launch_phase(const PhaseArgs<T> &a, int sms, cudaStream_t s);
+
 // Parameter checks shared by the single-run and the pool entry points.
 int validate_params(const pic_params *p);
 

@@ -5,13 +5,14 @@
 // field reads broadcasts and lets its deposit aggregate equal nodes before the
 // shared-memory atomics.  It changes no physical quantity.
 //
-// Four passes, all deterministic and stable (particles of one cell keep their
+// Five passes, all deterministic and stable (particles of one cell keep their
 // relative order):
 //   count    block b counts the cells of its contiguous chunk -> hist[b][g]
 //   colscan  per (segment of chunks, cell): exclusive prefix over the chunks
 //            of the segment, in place, and the segment total
-//   base     per cell: exclusive prefix over segments, in place; then the
-//            exclusive prefix of the cell totals over cells -> base[g]
+//   segscan  per cell: exclusive prefix over the segments, in place, and the
+//            cell total
+//   base     exclusive prefix of the cell totals over the cells -> base[g]
 //   scatter  block b walks its chunk in order, 256 particles at a time; the
 //            warps take their slots from the per-cell cursor one after the
 //            other, so the order within a cell is the original order.
@@ -42,8 +43,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_count_kernel(SortArgs<T> a)
     __syncthreads();
     const long long start = (long long)blockIdx.x * a.chunk;
     const long long end = min(a.n, start + a.chunk);
-    const int lane = threadIdx.x & 31;
-    constexpr int K = 4;
+    constexpr int K = 8;   // loads in flight per thread
     for (long long i0 = start; i0 < end; i0 += K * blockDim.x) {
         T xv[K];
 #pragma unroll
@@ -54,10 +54,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_count_kernel(SortArgs<T> a)
 #pragma unroll
         for (int k = 0; k < K; k++) {
             const long long i = i0 + k * blockDim.x + threadIdx.x;
-            const bool valid = i < end;
-            const unsigned key = valid ? cell_key(xv[k], a.inv_dx, ng) : kNoKey;
-            const unsigned peers = __match_any_sync(kFull, key);
-            if (valid && lane == __ffs(peers) - 1) atomicAdd(&sh_count[key], (unsigned)__popc(peers));
+            if (i < end) atomicAdd(&sh_count[cell_key(xv[k], a.inv_dx, ng)], 1u);
         }
     }
     __syncthreads();
@@ -84,6 +81,27 @@ __global__ void __launch_bounds__(256) sort_colscan_kernel(SortArgs<T> a) {
     a.segtot[(size_t)seg * a.ng + g] = run;
 }
 
+// Per cell: exclusive prefix of the segment totals over the segments (in
+// place) and the cell total (into base).  One thread per cell.
+template <typename T>
+__global__ void __launch_bounds__(256) sort_segscan_kernel(SortArgs<T> a) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= a.ng) return;
+    const int ng = a.ng;
+    unsigned c[kMaxSegLen];
+#pragma unroll
+    for (int s = 0; s < kMaxSegLen; s++) c[s] = s < a.nseg ? a.segtot[(size_t)s * ng + g] : 0u;
+    unsigned run = 0;
+#pragma unroll
+    for (int s = 0; s < kMaxSegLen; s++) {
+        if (s < a.nseg) a.segtot[(size_t)s * ng + g] = run;
+        run += c[s];
+    }
+    a.base[g] = run;
+}
+
+// Exclusive prefix of the cell totals over the cells -> first slot of each
+// cell.  One block; each thread scans a contiguous run of cells.
 template <typename T>
 __global__ void __launch_bounds__(512) sort_base_kernel(SortArgs<T> a) {
     __shared__ unsigned wt[32];
@@ -93,21 +111,9 @@ __global__ void __launch_bounds__(512) sort_base_kernel(SortArgs<T> a) {
     unsigned local = 0;
     for (int j = 0; j < k; j++) {
         const int g = g0 + j;
-        if (g >= ng) break;
-        unsigned c[kMaxSegLen];
-#pragma unroll
-        for (int s = 0; s < kMaxSegLen; s++) c[s] = s < a.nseg ? a.segtot[(size_t)s * ng + g] : 0u;
-        unsigned run = 0;
-#pragma unroll
-        for (int s = 0; s < kMaxSegLen; s++) {
-            if (s < a.nseg) a.segtot[(size_t)s * ng + g] = run;
-            run += c[s];
-        }
-        a.base[g] = run;   // cell total for now
-        local += run;
+        if (g < ng) local += a.base[g];
     }
-    // exclusive prefix of thread sums
-    const int lane = t & 31, w = t >> 5, nw = T_ >> 5;
+    const int lane = t & 31, w = t >> 5;
     unsigned inc = local;
     for (int o = 1; o < 32; o <<= 1) {
         const unsigned u = __shfl_up_sync(kFull, inc, o);
@@ -116,7 +122,7 @@ __global__ void __launch_bounds__(512) sort_base_kernel(SortArgs<T> a) {
     if (lane == 31) wt[w] = inc;
     __syncthreads();
     unsigned off = 0;
-    for (int i = 0; i < w && i < nw; i++) off += wt[i];
+    for (int i = 0; i < w; i++) off += wt[i];
     unsigned run = off + inc - local;
     for (int j = 0; j < k; j++) {
         const int g = g0 + j;
@@ -181,6 +187,8 @@ cudaError_t launch_sort_t(const SortArgs<T> &a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     dim3 cg((a.ng + 255) / 256, a.nseg);
     sort_colscan_kernel<T><<<cg, 256, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    sort_segscan_kernel<T><<<(a.ng + 255) / 256, 256, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     sort_base_kernel<T><<<1, 512, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -1,0 +1,57 @@
+"""Phase-space snapshots (the Sec. 4 two-stream test, Fig. 1): the device
+histogram against the same bin rule applied to the run's own particles, and
+the paper's observation that the beams mix by t = 20."""
+import math
+
+import numpy as np
+import pytest
+
+import paper_1108_1954_gb300 as pic  # noqa: E402
+import torch  # noqa: E402,F401
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+L4PI = 4.0 * math.pi
+
+
+def host_bins(x, v, nx, nv, L, vmin, vmax):
+    sx = np.float32(nx / L)
+    sv = np.float32(nv / (vmax - vmin))
+    fx = x.astype(np.float32) * sx
+    fv = np.floor((v.astype(np.float32) - np.float32(vmin)) * sv)
+    ok = (fx >= 0) & (fv >= 0) & (fv < nv)
+    ix = np.minimum(fx[ok].astype(np.int64), nx - 1)
+    iv = fv[ok].astype(np.int64)
+    out = np.zeros((nv, nx), dtype=np.uint32)
+    np.add.at(out, (iv, ix), 1)
+    return out
+
+
+@pytest.mark.parametrize("nx,nv", [(64, 64), (128, 100), (1, 1)])
+def test_phase_space_counts(nx, nv):
+    n = 100003
+    x, v = W.two_stream(n, L4PI, 0.2, 0.05, 3)
+    run = pic.Run(pic.Params(npart=n, ncell=64, length=L4PI), device="cuda:0")
+    run.init(*W.to_f32_state(x, v, L4PI))
+    run.step_n(7)
+    xs, vs = run.get_state()
+    got = run.phase_space(nx, nv, -0.5, 0.5)
+    assert np.array_equal(got, host_bins(xs, vs, nx, nv, L4PI, -0.5, 0.5))
+    with pytest.raises(pic.PicError):
+        run.phase_space(200, 200, -1.0, 1.0)           # above the bin limit
+
+
+def test_two_stream_beams_mix_by_t20():
+    # Fig. 1: at t = 0 two lines at v = +-0.2; at t = 20 vortices, with beam
+    # particles near v = 0 or moving the other way.
+    n = 20000
+    x, v = W.two_stream(n, L4PI, 0.2, 0.01, 11)
+    run = pic.Run(pic.Params(npart=n, ncell=64, length=L4PI), device="cuda:0")
+    run.init(*W.to_f32_state(x, v, L4PI))
+    f0 = run.phase_space(64, 40, -0.4, 0.4)
+    run.step_n(200)
+    f20 = run.phase_space(64, 40, -0.4, 0.4)
+    slow = slice(15, 25)                       # |v| < 0.1
+    assert f0[slow].sum() == 0
+    assert f20[slow].sum() > 0.2 * n
+    assert f0.sum() == n and f20.sum() <= n
