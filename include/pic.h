@@ -74,6 +74,17 @@ extern "C" {
 #define PIC_DEPOSIT_QUAD 5         /* runs within a thread's 4 particles,
                                       two atomics per run                  */
 
+/* Field solvers (pic_params.field_solver).  Both solve the Eq. 6 system with
+ * Phi_0 = 0 (the gauge the paper pins).
+ *   EXACT  the converged solution, by exact prefix sums (default);
+ *   CG     the paper's solver (Sec. 2.2, Sec. 3.3, Appendix A): matrix-free
+ *          conjugate gradient from Phi = 0, a fixed number of iterations
+ *          (the paper forces 150), float64, unconverged field included.
+ *          Single runs only (the pool rejects it with PIC_EINVAL). */
+#define PIC_SOLVER_EXACT 0
+#define PIC_SOLVER_CG 1
+#define PIC_CG_DEFAULT_ITERATIONS 150
+
 #define PIC_NCELL_MAX 8192  /* largest NG (the per-block density tile)       */
 #define PIC_NMODES 8        /* Fourier modes recorded per step               */
 
@@ -94,6 +105,10 @@ typedef struct pic_params {
     int32_t blocks_per_sm; /* resident blocks per SM of the fused push (0=auto)*/
     int32_t unroll;        /* float4 groups per thread per iteration of the
                               fused push: 1, 2, 4 (0 = auto)                 */
+    int32_t field_solver;  /* PIC_SOLVER_EXACT | PIC_SOLVER_CG                 */
+    int32_t cg_iterations; /* PIC_SOLVER_CG: iterations per solve, run to the
+                              end whether converged or not (0 = 150, the
+                              paper's fixed count; at most 100000)           */
 } pic_params;
 
 /* One row of the per-step diagnostics (all float64 on the device). */

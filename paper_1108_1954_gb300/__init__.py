@@ -31,6 +31,8 @@ PIC_ETIMEOUT, PIC_EDEVICE, PIC_ESTATE = -4, -5, -6
 PIC_FP32_FIXED, PIC_FP32_ATOMIC, PIC_FP64 = 0, 1, 2
 PIC_DEPOSIT_AUTO, PIC_DEPOSIT_ATOMIC, PIC_DEPOSIT_MATCH = 0, 1, 2
 PIC_DEPOSIT_PACKED, PIC_DEPOSIT_MATCH_PACKED, PIC_DEPOSIT_QUAD = 3, 4, 5
+PIC_SOLVER_EXACT, PIC_SOLVER_CG = 0, 1
+PIC_CG_DEFAULT_ITERATIONS = 150
 PIC_NCELL_MAX = 8192
 PIC_NMODES = 8
 FIX_BITS = 24
@@ -48,7 +50,8 @@ class CParams(C.Structure):
                 ("rho_ion", C.c_double), ("sort_interval", C.c_int32),
                 ("history", C.c_int32), ("deposit_variant", C.c_int32),
                 ("block_size", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("unroll", C.c_int32)]
+                ("unroll", C.c_int32), ("field_solver", C.c_int32),
+                ("cg_iterations", C.c_int32)]
 
 
 class CDiagRow(C.Structure):
@@ -160,6 +163,8 @@ class Params:
     block_size: int = 0
     blocks_per_sm: int = 0
     unroll: int = 0
+    field_solver: int = 0          # PIC_SOLVER_EXACT
+    cg_iterations: int = 0         # 0: the paper's 150
 
     def c(self) -> CParams:
         return CParams(int(self.npart), int(self.ncell), int(self.precision),
@@ -167,7 +172,8 @@ class Params:
                        float(self.rho_ion), int(self.sort_interval),
                        int(self.history), int(self.deposit_variant),
                        int(self.block_size), int(self.blocks_per_sm),
-                       int(self.unroll))
+                       int(self.unroll), int(self.field_solver),
+                       int(self.cg_iterations))
 
     @property
     def dtype(self):

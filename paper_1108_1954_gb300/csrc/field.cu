@@ -21,14 +21,15 @@
 // and float64 arithmetic appears only in the final conversion of each value,
 // so E is within an ulp or two of the exactly rounded solution.  GB300 runs
 // float64 at a small fraction of its float32 rate; this keeps the solve cheap.
-// The nodes are split over up to 32 blocks; each block forms the global sums
-// it needs (sum_k P_k and the prefixes up to its first node) as weighted
-// integer reductions over the whole grid, then converts its own nodes.  The
-// last block to finish (an atomic ticket, no waiting) reduces the per-block
-// diagnostics in a fixed order, writes the history rows, clears the density
-// accumulator and advances the step counter.
+// The nodes are split over the blocks of one thread-block cluster (one node
+// per thread); the blocks exchange their slice sums through distributed
+// shared memory, and block 0 reduces the diagnostics and writes the history
+// rows.
 //
-// Float modes (precision study): one block, float64 prefix scans of rho.
+// Float modes (precision study): one block, float64 prefix scans of rho; the
+// block then reduces the diagnostics, writes the history rows, clears the
+// density accumulator and advances the step counter (finalize).  The paper's
+// CG solver (PIC_SOLVER_CG) runs the same way in one block.
 //
 // Diagnostics: field energy (1/2) dx sum E^2 in float64; mode amplitudes
 // from the float32 field with float32 twiddles, summed per block in float32
@@ -36,10 +37,17 @@
 // per-block float64 sums, reduced in a fixed order.
 #include <math.h>
 
+#include <cooperative_groups.h>
+
 #include "field_ops.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace pic {
 namespace {
+
+constexpr int kClusterSolveThreads = 512;   // nodes per block (one per thread)
+constexpr int kMaxSolveCluster = 16;        // blocks per cluster (16: non-portable)
 
 // The block's share of the diagnostics, written to a.dpart[blockIdx.x]; the
 // push's per-block sums are split over the solve blocks.
@@ -135,105 +143,430 @@ __device__ void finalize(const SolveArgs &a, long long step) {
     }
 }
 
-// ---- fixed-point solve: exact integer prefix sums --------------------------
+// ---- the cluster solves' common parts -------------------------------------
 
-__global__ void __launch_bounds__(256) pic_solve_fixed_kernel(SolveArgs a) {
-    __shared__ i128 sh[96];
-    const int ng = a.ng, T = blockDim.x, t = threadIdx.x;
-    const long long step = *a.dstep;
-    const long long ntot = a.weight_total;   // N 2^24
-    const int per = (ng + gridDim.x - 1) / gridDim.x;   // nodes per block (<= T)
-    const int b0 = blockIdx.x * per;
-    const int b1 = min(ng, b0 + per);
-
-    // (a) global weighted sums of R over the whole grid:
-    //   A0 = sum_{k<b0} R_k, A1 = sum_{k<b0} (b0-k) R_k   (prefixes to b0)
-    //   SP = sum_k (NG-k) R_k = sum_g P_g,  also sum_k R_k (= P_{NG-1}).
-    i128 A0 = 0, A1 = 0, SP = 0, SR = 0;
-    {
-        constexpr int kBatch = 8;   // loads in flight per thread
-        for (int k0 = t; k0 < ng; k0 += kBatch * T) {
-            unsigned long long q[kBatch];
+// Sum of one float64 per thread over a block (warp trees, then warp 0 over
+// the warp sums); valid in lane 0 of warp 0.  Adds in predicated lanes only,
+// since float64 issue is scarce on GB300.
+__device__ __forceinline__ double block_sum_f64(double v, double *slot /*[32]*/) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-            for (int i = 0; i < kBatch; i++) {
-                const int k = k0 + i * T;
-                q[i] = k < ng ? __ldcg(&a.rho_q[k]) : 0ull;
-            }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double u = __shfl_down_sync(kFull, v, o);
+        if (lane < o) v += u;
+    }
+    if (lane == 0) slot[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (w == 0) {
+        s = lane < nw ? slot[lane] : 0.0;
 #pragma unroll
-            for (int i = 0; i < kBatch; i++) {
-                const int k = k0 + i * T;
-                if (k < ng) {
-                    const i128 R = (i128)ntot - (i128)ng * (i128)q[i];
-                    SP += R * (long long)(ng - k);
-                    SR += R;
-                    const bool before = k < b0;
-                    A0 += before ? R : (i128)0;
-                    A1 += before ? R * (long long)(b0 - k) : (i128)0;
-                }
-            }
+        for (int o = 16; o > 0; o >>= 1) {
+            if (o >= nw) continue;            // warp-uniform: only the levels nw needs
+            const double u = __shfl_down_sync(kFull, s, o);
+            if (lane < o) s += u;
         }
     }
-    block_sum3_i128(A0, A1, SP, sh);
-    {
-        i128 z1 = 0, z2 = 0;
-        block_sum3_i128(SR, z1, z2, sh);
-    }
+    return s;
+}
 
-    // (b) the block's nodes: one per thread
+// Sum over the cluster of the blocks' values *pub (each published by its
+// block before the caller's cluster barrier), the same fixed tree over the
+// ranks in every warp of every block: every thread gets the same total.
+__device__ __forceinline__ double cluster_total(cg::cluster_group &cl, const double *pub, int C) {
+    const int lane = threadIdx.x & 31;
+    double p = lane < C ? *cl.map_shared_rank(pub, lane) : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        if (o >= C) continue;                 // uniform: only the levels C needs
+        const double u = __shfl_down_sync(kFull, p, o);
+        if (lane < o) p += u;
+    }
+    return __shfl_sync(kFull, p, 0);
+}
+
+// The part of a block's shared memory that block 0 reads for the diagnostics.
+struct ClusterDiag {
+    double kv[2];                 // the block's share of the push sums
+    double diag[kDiagFields];     // slice diagnostics
+    unsigned long long cq;        // slice sum of rho_q
+};
+
+// The block's share of the push's per-block sums (summed over the block;
+// valid in warp 0).  Issued first in the solves, so the loads overlap.
+__device__ __forceinline__ void push_sums_share(const SolveArgs &a, int C, int r, double (&kv)[2],
+                                                double *shd) {
+    kv[0] = 0.0;
+    kv[1] = 0.0;
+    for (int i = r * blockDim.x + threadIdx.x; i < a.npartials; i += C * blockDim.x) {
+        kv[0] += a.partials[2 * i];
+        kv[1] += a.partials[2 * i + 1];
+    }
+    block_sum_t<2, double>(kv, shd);
+}
+
+// Diagnostics of a cluster solve: block sums of the nodes' contributions,
+// then block 0 sums the blocks in rank order (after a cluster barrier) and
+// writes the history rows (scalars by thread 0, mode m by thread m); a last
+// cluster barrier keeps every block's shared memory alive until block 0 has
+// read it.  charge: this block's share of the charge diagnostic.
+__device__ void cluster_finish(const SolveArgs &a, cg::cluster_group &cl, ClusterDiag &cd,
+                               const double (&kv)[2], const NodeDiag &d, double charge,
+                               unsigned long long q, long long step) {
+    __shared__ double shd[32];
+    __shared__ float shf[32 * 2 * PIC_NMODES];
+    __shared__ unsigned long long cqw[32];
+    const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
+    const int T = blockDim.x, t = threadIdx.x, lane = t & 31;
+    double dv[1] = {d.fe};
+    block_sum_t<1, double>(dv, shd);
+    float md[2 * PIC_NMODES];
+#pragma unroll
+    for (int m = 0; m < PIC_NMODES; m++) { md[2 * m] = d.re[m]; md[2 * m + 1] = d.im[m]; }
+    block_sum_t<2 * PIC_NMODES, float>(md, shf);
+    unsigned long long cqb = q;
+    for (int o = 16; o > 0; o >>= 1) cqb += __shfl_down_sync(kFull, cqb, o);
+    if (lane == 0) cqw[t >> 5] = cqb;
+    __syncthreads();
+    if (t < 32) {
+        // lane m of warp 0 stores value m (md is complete in warp 0)
+        float mine = 0.0f;
+#pragma unroll
+        for (int m = 0; m < 2 * PIC_NMODES; m++) mine = (m == t) ? md[m] : mine;
+        if (t < 2 * PIC_NMODES) cd.diag[kDiagModes + t] = (double)mine;
+        if (t == 0) {
+            unsigned long long s = 0;
+            for (int w = 0; w < (T >> 5); w++) s += cqw[w];
+            cd.cq = s;
+            cd.kv[0] = kv[0];
+            cd.kv[1] = kv[1];
+            cd.diag[kDiagFE] = dv[0];
+            cd.diag[kDiagKE] = 0.0;
+            cd.diag[kDiagMom] = 0.0;
+            cd.diag[kDiagCharge] = charge;
+        }
+    }
+    cl.sync();
+    if (r == 0) {
+        // field f summed over the blocks in rank order by thread f
+        __shared__ double tot[kDiagFields + 2];
+        __shared__ unsigned long long tot_cq;
+        if (t < kDiagFields + 2) {
+            double part[kMaxSolveCluster];
+#pragma unroll
+            for (int b = 0; b < kMaxSolveCluster; b++) {
+                const ClusterDiag *pe = cl.map_shared_rank(&cd, b < C ? b : 0);
+                part[b] = b >= C ? 0.0 : (t < kDiagFields ? pe->diag[t] : pe->kv[t - kDiagFields]);
+            }
+            double acc = 0.0;
+#pragma unroll
+            for (int b = 0; b < kMaxSolveCluster; b++) acc += part[b];
+            tot[t] = acc;
+        } else if (t == kDiagFields + 2) {
+            unsigned long long acc = 0;
+            for (int b = 0; b < C; b++) acc += cl.map_shared_rank(&cd, b)->cq;
+            tot_cq = acc;
+        }
+        __syncthreads();
+        const long long n = a.npartials > 0 ? step + 1 : step;
+        pic_diag_row *row = &a.hist[n % a.hist_len];
+        if (t == 0) {
+            if (a.npartials > 0) {
+                pic_diag_row *prev = &a.hist[step % a.hist_len];
+                prev->kinetic = 0.5 * a.mass * tot[kDiagFields];
+                prev->momentum = a.mass * tot[kDiagFields + 1];
+                *a.dstep = n;
+            }
+            const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+            row->step = n;
+            row->kinetic = qnan;
+            row->momentum = qnan;
+            row->field = 0.5 * a.dx * tot[kDiagFE];
+            row->charge = tot[kDiagCharge];
+            row->charge_q = (long long)tot_cq;
+        }
+        if (t < PIC_NMODES) {
+            const double re = tot[kDiagModes + 2 * t], im = tot[kDiagModes + 2 * t + 1];
+            row->mode[t] = 2.0 * sqrt(re * re + im * im) / (double)a.ng;
+        }
+    }
+    cl.sync();
+}
+
+// ---- fixed-point solve on one thread-block cluster --------------------------
+//
+// The same exact integer solve with the nodes split into C <= 16 slices of
+// ceil(NG/C) nodes: one slice per block of a cluster, one node per thread.
+// Each block reads (and clears) only its own slice of the accumulator and
+// publishes its slice sums sum_k R_k and sum_k k R_k in shared memory.  After
+// a cluster barrier every block forms, from all slices' sums (one remote read
+// per lane of warp 0; integer sums, so the order does not matter),
+//   A0 = sum_{k<b0} R_k,  A1 = b0 A0 - sum_{k<b0} k R_k,
+//   SR = sum_k R_k,       SP = NG SR - sum_k k R_k,
+// and solves its slice with two block-wide scans as above; then the
+// diagnostics (cluster_finish).  Three cluster barriers, no global atomics.
+struct SliceSums {
+    i128 s0, s1;                  // slice sums of R and k R
+};
+
+__global__ void __launch_bounds__(kClusterSolveThreads) pic_solve_cluster_kernel(SolveArgs a) {
+    cg::cluster_group cl = cg::this_cluster();
+    __shared__ SliceSums ex;
+    __shared__ ClusterDiag cd;
+    __shared__ i128 sh[96];
+    __shared__ i128 wlast[32];
+    __shared__ i128 pre[4];
+    __shared__ double shd[32 * 2];
+    const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
+    const int ng = a.ng, t = threadIdx.x, lane = t & 31;
+    const long long step = *a.dstep;
+    const long long ntot = a.weight_total;
+    const int per = (ng + C - 1) / C;
+    const int b0 = r * per;
+    const int b1 = min(ng, b0 + per);
     const int g = b0 + t;
     const bool mine = g < b1;
-    const unsigned long long q = mine ? a.rho_q[g] : 0ull;
-    const i128 R = mine ? (i128)ntot - (i128)ng * (i128)q : (i128)0;
-    i128 tot;
-    const i128 P = A0 + block_inclusive_scan_i128(R, sh, tot);  // P_g
-    const i128 M = (i128)ng * P - SP;                          // M_g
-    // M_{g-1}: previous thread, or for the block's first node the prefix to b0
-    i128 Mprev = shfl_up_i128(M, 1);
-    __shared__ i128 wlast[32];
-    if ((t & 31) == 31) wlast[t >> 5] = M;
-    __syncthreads();
-    if ((t & 31) == 0) {
-        if (t == 0) {
-            // M_{b0-1} = NG P_{b0-1} - SP with P_{b0-1} = A0; b0 = 0 wraps to
-            // M_{NG-1} = NG SR - SP
-            Mprev = (b0 == 0) ? (i128)ng * SR - SP : (i128)ng * A0 - SP;
-        } else {
-            Mprev = wlast[(t >> 5) - 1];
-        }
+    unsigned long long q = 0ull;
+    if (mine) {
+        q = __ldcg(&a.rho_q[g]);
+        a.rho_q[g] = 0ull;            // read by this thread only
+        a.rho_q_last[g] = q;
     }
-    // sum_{k<g} M_k = NG sum_{k<g} P_k - g SP, with
-    // sum_{k<g} P_k = (sum_{k<b0} P_k) + exclusive block prefix of P
-    //               = (b0 A0 - A1 + A0... ) computed as below.
-    // sum_{k<b0} P_k = sum_{k<b0} sum_{j<=k} R_j = sum_{j<b0} (b0 - j) R_j = A1.
-    i128 ptot;
-    const i128 Pexcl = block_inclusive_scan_i128(mine ? P : (i128)0, sh, ptot) - (mine ? P : (i128)0);
-    const i128 sumM = (i128)ng * (A1 + Pexcl) - (i128)g * SP;
+    double kv[2];
+    push_sums_share(a, C, r, kv, shd);
+    const i128 R = mine ? (i128)ntot - (i128)ng * (i128)q : (i128)0;
+    {
+        i128 S0 = R, S1 = R * (i128)g, Sz = 0;
+        block_sum3_i128(S0, S1, Sz, sh);
+        if (t == 0) { ex.s0 = S0; ex.s1 = S1; }
+    }
+    cl.sync();                                                        // #1
 
+    if (t < 32) {
+        i128 v0 = 0, v1 = 0;
+        if (t < C) {
+            const SliceSums *pe = cl.map_shared_rank(&ex, t);
+            v0 = pe->s0;
+            v1 = pe->s1;
+        }
+        i128 a0 = t < r ? v0 : (i128)0, bb = t < r ? v1 : (i128)0;
+        for (int o = 16; o > 0; o >>= 1) {
+            a0 += shfl_down_i128(a0, o);
+            bb += shfl_down_i128(bb, o);
+            v0 += shfl_down_i128(v0, o);
+            v1 += shfl_down_i128(v1, o);
+        }
+        if (t == 0) { pre[0] = a0; pre[1] = bb; pre[2] = v0; pre[3] = v1; }
+    }
+    __syncthreads();
+    const i128 A0 = pre[0], B = pre[1], SR = pre[2], SS1 = pre[3];
+    const i128 SP = (i128)ng * SR - SS1;          // sum_k (NG-k) R_k
+    const i128 A1 = (i128)b0 * A0 - B;             // sum_{k<b0} (b0-k) R_k
+    i128 tot_;
+    const i128 P = A0 + block_inclusive_scan_i128(R, sh, tot_);        // P_g
+    const i128 Pin = mine ? P : (i128)0;
+    const i128 pex = block_inclusive_scan_i128(Pin, sh, tot_) - Pin;    // sum_{b0<=k<g} P_k
+    const i128 M = (i128)ng * P - SP;                                  // M_g
+    i128 Mprev = shfl_up_i128(M, 1);
+    if (lane == 31) wlast[t >> 5] = M;
+    __syncthreads();
+    if (lane == 0)
+        Mprev = t == 0 ? (b0 == 0 ? (i128)ng * SR - SP : (i128)ng * A0 - SP)
+                       : wlast[(t >> 5) - 1];
     NodeDiag d;
     node_diag_reset(d);
     if (mine) {
-        const double rho = a.k_rho * i128_to_f64(R);
+        const i128 sumM = (i128)ng * (A1 + pex) - (i128)g * SP;
         const double E = a.k_e * i128_to_f64(M + Mprev);
-        const double phi = a.k_phi * i128_to_f64(sumM);
         const float E32 = (float)E;
-        a.rho[g] = rho;
+        a.rho[g] = a.k_rho * i128_to_f64(R);
         a.E64[g] = E;
         a.E32[g] = E32;
-        a.phi[g] = phi;
-        a.rho_q_last[g] = q;
+        a.phi[g] = a.k_phi * i128_to_f64(sumM);
         node_diag(d, g, ng, E, E32);
     }
-    // charge of the block's nodes, exactly: dx K sum R (block 0 reports all)
-    const double charge = (blockIdx.x == 0) ? a.dx * a.k_rho * i128_to_f64(SR) : 0.0;
-    unsigned long long cq = q;
-    for (int o = 16; o > 0; o >>= 1) cq += __shfl_down_sync(kFull, cq, o);
-    __shared__ unsigned long long cqw[32];
-    if ((t & 31) == 0) cqw[t >> 5] = cq;
+    const double charge = r == 0 ? a.dx * a.k_rho * i128_to_f64(SR) : 0.0;
+    cluster_finish(a, cl, cd, kv, d, charge, q, step);                // #2, #3
+}
+
+// ---- CG: the paper's field solver, on one thread-block cluster ------------
+//
+// Sec. 2.2 / Sec. 3.3 / Appendix A: the matrix-free conjugate gradient on the
+// Eq. 6 system with Phi_0 = 0 pinned (row 0 the identity) and the last row
+// taking Phi_NG = 0, from x = 0 with r = v = -rho dx^2 (r_0 = v_0 = 0),
+// c = r.r; while the initial |r| > 1e-16, exactly maxit iterations of
+//   z = A v, t = c / (z.v), x += t v, r -= t z, d = r.r, v = (d/c) v + r, c = d
+// (the paper forces 150 and keeps the unconverged field).  Where the next
+// step would divide by zero (z.v == 0, t not finite, d == 0) it stops early.
+// Then Phi = x and E by Eq. 7 with periodic neighbours.  For a neutral box
+// the converged x is the periodic solution in the Phi_0 = 0 gauge.
+//
+// The nodes are split over the blocks of one cluster, one node per thread,
+// C = ceil(NG/32) <= 16 blocks: float64 issue (2 lanes per clock per SM on
+// GB300) rather than threads bounds an iteration, so the nodes are spread
+// over as many SMs as a cluster holds.  Float64 throughout.  Per iteration two cluster-wide
+// sums (z.v and r.r): block sums, published in shared memory, then every
+// warp adds the C block sums in the same fixed tree, so every thread of every
+// block holds the same scalars.  The two neighbour values of v that A v needs
+// from other blocks are not exchanged after the update: each block publishes
+// its boundary v (before the update) and r (after it) with r.r, and the
+// neighbour forms beta v + r itself -- the same operation on the same numbers
+// as the owner.  So an iteration has two cluster barriers.  A published value
+// is read after the barrier that follows its write and rewritten only after
+// the next barrier, which every reader passes after reading it.  Divisions
+// are done by one lane per warp (float64 division is a long sequence).
+struct CgExchange {
+    double zv, rr;                // block sums
+    double v0, v1, r0, r1;        // v (before the update) and r (after) at the
+                                  // slice's first and last node
+    double x0, x1;                // Phi at the slice's first and last node
+    i128 sr;                      // fixed point: slice sum of R
+};
+
+__device__ __forceinline__ double warp_div(double num, double den) {
+    double q = 0.0;
+    if ((threadIdx.x & 31) == 0) q = num / den;
+    return __shfl_sync(kFull, q, 0);
+}
+
+__global__ void __launch_bounds__(kClusterSolveThreads) pic_solve_cg_kernel(SolveArgs a) {
+    cg::cluster_group cl = cg::this_cluster();
+    __shared__ double sv[kClusterSolveThreads + 2];   // v of the slice, ghost-padded
+    __shared__ CgExchange ex;
+    __shared__ ClusterDiag cd;
+    __shared__ double slot[32];
+    __shared__ double shd[32 * 2];
+    __shared__ i128 sh[96];
+    const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
+    const int ng = a.ng, t = threadIdx.x;
+    const long long step = *a.dstep;
+    const double dx = a.dx;
+    const int per = (ng + C - 1) / C;
+    const int b0 = r * per;
+    const int cnt = min(ng, b0 + per) - b0;
+    const int g = b0 + t;
+    const bool mine = t < cnt;
+    double kv[2];
+    push_sums_share(a, C, r, kv, shd);
+    double rh = 0.0;
+    unsigned long long q = 0ull;
+    i128 R = 0;
+    if (mine) {
+        if (a.mode == PIC_FP32_FIXED) {
+            q = __ldcg(&a.rho_q[g]);
+            a.rho_q[g] = 0ull;
+            a.rho_q_last[g] = q;
+            R = (i128)a.weight_total - (i128)ng * (i128)q;
+            rh = a.k_rho * i128_to_f64(R);
+        } else if (a.mode == PIC_FP32_ATOMIC) {
+            const float acc = a.rho_f32[g];
+            a.rho_f32[g] = 0.0f;
+            rh = a.rho_ion + a.q_over_dx * (double)acc;
+        } else {
+            const double acc = a.rho_f64[g];
+            a.rho_f64[g] = 0.0;
+            rh = a.rho_ion + a.q_over_dx * acc;
+        }
+        a.rho[g] = rh;
+    }
+    if (a.mode == PIC_FP32_FIXED) {
+        i128 z1 = 0, z2 = 0, sr = R;
+        block_sum3_i128(sr, z1, z2, sh);
+        if (t == 0) ex.sr = sr;
+    }
+    double xg = 0.0;
+    double rg = (mine && g >= 1) ? (-rh * dx) * dx : 0.0;
+    double vg = rg;
+    if (mine) sv[t + 1] = vg;
+    if (t == 0) ex.v0 = vg;
+    if (t == cnt - 1) ex.v1 = vg;
+    {
+        const double s = block_sum_f64(rg * rg, slot);
+        if (t == 0) ex.rr = s;
+    }
+    cl.sync();
+    double c = cluster_total(cl, &ex.rr, C);
+    // the neighbours' boundary v (v = r at the start)
+    if (t == 0 && r > 0) sv[0] = cl.map_shared_rank(&ex, r - 1)->v1;
+    if (t == cnt - 1 && r < C - 1) sv[cnt + 1] = cl.map_shared_rank(&ex, r + 1)->v0;
     __syncthreads();
-    cq = 0;
-    for (int i = 0; i < (T >> 5); i++) cq += cqw[i];
-    write_block_partials(a, d, charge, cq);
-    finalize(a, step);
+    if (sqrt(c) > 1e-16 && ng > 1) {
+        for (int it = 0; it < a.cg_maxit; it++) {
+            double z = 0.0;
+            if (mine) {
+                const double vl = sv[t], vc = sv[t + 1], vr = sv[t + 2];
+                z = g == 0 ? vc : (g == ng - 1 ? vl - 2.0 * vc : (vl - 2.0 * vc) + vr);
+            }
+            {
+                const double s = block_sum_f64(z * vg, slot);
+                if (t == 0) ex.zv = s;
+            }
+            cl.sync();                                                // S1
+            const double dotzv = cluster_total(cl, &ex.zv, C);
+            if (!(dotzv != 0.0)) break;
+            const double tk = warp_div(c, dotzv);
+            if (!isfinite(tk)) break;
+            if (mine) {
+                xg = fma(tk, vg, xg);
+                rg = fma(-tk, z, rg);
+            }
+            if (t == 0) { ex.v0 = vg; ex.r0 = rg; }
+            if (t == cnt - 1) { ex.v1 = vg; ex.r1 = rg; }
+            {
+                const double s = block_sum_f64(rg * rg, slot);
+                if (t == 0) ex.rr = s;
+            }
+            cl.sync();                                                // S2
+            const double d = cluster_total(cl, &ex.rr, C);
+            if (!(d > 0.0)) break;
+            const double beta = warp_div(d, c);
+            if (mine) {
+                vg = fma(beta, vg, rg);
+                sv[t + 1] = vg;
+            }
+            if (t == 0 && r > 0) {
+                const CgExchange *pl = cl.map_shared_rank(&ex, r - 1);
+                sv[0] = fma(beta, pl->v1, pl->r1);
+            }
+            if (t == cnt - 1 && r < C - 1) {
+                const CgExchange *pr = cl.map_shared_rank(&ex, r + 1);
+                sv[cnt + 1] = fma(beta, pr->v0, pr->r0);
+            }
+            c = d;
+            __syncthreads();
+        }
+    }
+    // Phi = x; E by Eq. 7 with periodic neighbours (across the blocks)
+    __syncthreads();
+    if (mine) sv[t + 1] = xg;
+    if (t == 0) ex.x0 = xg;
+    if (t == cnt - 1) ex.x1 = xg;
+    cl.sync();
+    if (t == 0) sv[0] = cl.map_shared_rank(&ex, r > 0 ? r - 1 : C - 1)->x1;
+    if (t == cnt - 1) sv[cnt + 1] = cl.map_shared_rank(&ex, r < C - 1 ? r + 1 : 0)->x0;
+    __syncthreads();
+    NodeDiag dg;
+    node_diag_reset(dg);
+    double pcharge = 0.0;
+    if (mine) {
+        const double E = -(sv[t + 2] - sv[t]) / (2.0 * dx);
+        const float E32 = (float)E;
+        a.phi[g] = xg;
+        a.E64[g] = E;
+        a.E32[g] = E32;
+        node_diag(dg, g, ng, E, E32);
+        pcharge = rh;
+    }
+    double charge;
+    if (a.mode == PIC_FP32_FIXED) {
+        i128 sr = 0;
+        if (r == 0)
+            for (int b = 0; b < C; b++) sr += cl.map_shared_rank(&ex, b)->sr;
+        charge = r == 0 ? dx * a.k_rho * i128_to_f64(sr) : 0.0;
+    } else {
+        charge = dx * block_sum_f64(pcharge, slot);
+    }
+    cluster_finish(a, cl, cd, kv, dg, charge, q, step);
 }
 
 // ---- float modes: one block, float64 prefix scans ---------------------------
@@ -331,23 +664,47 @@ __global__ void __launch_bounds__(kSolveThreads) pic_solve_float_kernel(SolveArg
 
 }  // namespace
 
-int solve_blocks(int mode, int ng) {
-    if (mode != PIC_FP32_FIXED) return 1;
-    int nb = (ng + kSolveThreads - 1) / kSolveThreads;   // at least NG/T nodes each
-    const int want = (ng + 255) / 256;                   // about 256 nodes per block
-    if (want > nb) nb = want;
-    return nb < kSolveMaxBlocks ? nb : kSolveMaxBlocks;
+
+// Cluster shape of the solves: C = ceil(NG / per_block) blocks (at most 16),
+// ceil(NG / C) nodes each, rounded up to whole warps.  The exact solve takes
+// up to 512 nodes per block, the CG 32 (its iterations are float64-bound).
+void solve_cluster_shape(int ng, int per_block, int *C, int *threads) {
+    int c = (ng + per_block - 1) / per_block;
+    c = c < 1 ? 1 : (c > kMaxSolveCluster ? kMaxSolveCluster : c);
+    const int per = (ng + c - 1) / c;
+    *C = c;
+    *threads = ((per + 31) / 32) * 32;
+}
+
+cudaError_t solve_prepare_attributes() {
+    cudaError_t e = cudaFuncSetAttribute(&pic_solve_cluster_kernel,
+                                         cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(&pic_solve_cg_kernel,
+                                cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
 
 cudaError_t launch_solve(const SolveArgs &a, cudaStream_t s) {
-    if (a.mode == PIC_FP32_FIXED) {
-        const int nb = solve_blocks(a.mode, a.ng);
-        const int per = (a.ng + nb - 1) / nb;
-        const int threads = ((per + 31) / 32) * 32;
-        pic_solve_fixed_kernel<<<nb, threads < 32 ? 32 : threads, 0, s>>>(a);
-    } else {
-        pic_solve_float_kernel<<<1, kSolveThreads, 0, s>>>(a);
+    if (a.solver == PIC_SOLVER_CG || a.mode == PIC_FP32_FIXED) {
+        int C = 1, threads = 32;
+        solve_cluster_shape(a.ng, a.solver == PIC_SOLVER_CG ? 32 : kClusterSolveThreads, &C,
+                            &threads);
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        cfg.gridDim = dim3((unsigned)C, 1, 1);
+        cfg.blockDim = dim3((unsigned)threads, 1, 1);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (a.solver == PIC_SOLVER_CG) return cudaLaunchKernelEx(&cfg, pic_solve_cg_kernel, a);
+        return cudaLaunchKernelEx(&cfg, pic_solve_cluster_kernel, a);
     }
+    pic_solve_float_kernel<<<1, kSolveThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

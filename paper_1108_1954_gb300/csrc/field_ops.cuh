@@ -70,9 +70,11 @@ static __device__ void block_sum3_i128(i128 &a, i128 &b, i128 &c, i128 *sh /*[96
     __syncthreads();
 }
 
-// Block sum of K values per thread, fixed order; result valid in thread 0.
-// Warp sums by shuffles; the cross-warp sum of value i by lane i of warp 0
-// (all lanes in parallel), then gathered to thread 0.
+// Block sum of K values per thread, fixed order; result valid in thread 0
+// (in fact in every lane of warp 0).  Warp sums by shuffles; the cross-warp
+// sum of each value by warp 0: for float64 (a slow pipe on GB300, so the
+// dependent chain matters) a butterfly over the warp sums, one value at a
+// time; for float32 lane i adds value i over the warps.
 template <int K, typename T>
 static __device__ void block_sum_t(T (&v)[K], T *sh /*[32*K]*/) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -85,11 +87,20 @@ static __device__ void block_sum_t(T (&v)[K], T *sh /*[32*K]*/) {
     __syncthreads();
     if (w == 0) {
         static_assert(K <= 32, "one lane per value");
-        T s = 0;
-        if (lane < K)
-            for (int j = 0; j < nw; j++) s += sh[j * K + lane];
+        if (sizeof(T) == 8) {
 #pragma unroll
-        for (int i = 0; i < K; i++) v[i] = __shfl_sync(kFull, s, i);
+            for (int i = 0; i < K; i++) {
+                T s = lane < nw ? sh[lane * K + i] : (T)0;
+                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+                v[i] = s;
+            }
+        } else {
+            T s = 0;
+            if (lane < K)
+                for (int j = 0; j < nw; j++) s += sh[j * K + lane];
+#pragma unroll
+            for (int i = 0; i < K; i++) v[i] = __shfl_sync(kFull, s, i);
+        }
     }
     __syncthreads();
 }

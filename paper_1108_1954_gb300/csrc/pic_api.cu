@@ -43,6 +43,8 @@ int pic::validate_params(const pic_params *p) {
     if (p->precision == PIC_FP32_FIXED && p->block_size > 512) return PIC_EINVAL;
     if (p->blocks_per_sm < 0 || p->blocks_per_sm > 32) return PIC_EINVAL;
     if (p->unroll != 0 && p->unroll != 1 && p->unroll != 2 && p->unroll != 4) return PIC_EINVAL;
+    if (p->field_solver != PIC_SOLVER_EXACT && p->field_solver != PIC_SOLVER_CG) return PIC_EINVAL;
+    if (p->cg_iterations < 0 || p->cg_iterations > 100000) return PIC_EINVAL;
     return PIC_OK;
 }
 
@@ -67,17 +69,21 @@ struct DevScalars {
     unsigned counter;
 };
 
-void sort_geometry(int64_t n, int *nchunk, long long *chunk, int *nseg, int *seg_len) {
+// Chunks of the counting sort: 2048 particles (one scatter tile) or more
+// each, at most kMaxSortChunks, and at most 32 MiB of per-chunk counts;
+// segments of about sqrt(nchunk) chunks.
+void sort_geometry(int64_t n, int ng, int *nchunk, long long *chunk, int *nseg, int *seg_len) {
     long long nc = (n + 2047) / 2048;
-    if (nc < 1) nc = 1;
+    const long long cap_tab = (32ll << 20) / (4ll * ng);
     if (nc > kMaxSortChunks) nc = kMaxSortChunks;
+    if (nc > cap_tab) nc = cap_tab;
+    if (nc < 1) nc = 1;
     long long ch = (n + nc - 1) / nc;
     nc = (n + ch - 1) / ch;
     int ns = 1;
     while ((long long)ns * ns < nc) ns++;   // nseg, seg_len <= 32 (nchunk <= 1024)
     *nchunk = (int)nc;
     *chunk = ch;
-    *nseg = ns;
     *seg_len = (int)((nc + ns - 1) / ns);
     *nseg = (int)((nc + *seg_len - 1) / *seg_len);
 }
@@ -106,7 +112,7 @@ void make_layout(const pic_params *p, Layout *L) {
     L->dev = take(sizeof(DevScalars));
     L->tune_rho = take(ng * 8);
     L->phase = take((size_t)kPhaseMaxBins * 4);
-    sort_geometry(p->npart, &L->nchunk, &L->chunk, &L->nseg, &L->seg_len);
+    sort_geometry(p->npart, p->ncell, &L->nchunk, &L->chunk, &L->nseg, &L->seg_len);
     L->s_hist = take((size_t)L->nchunk * ng * 4);
     L->s_segtot = take((size_t)L->nseg * ng * 4);
     L->s_base = take(ng * 4);
@@ -135,7 +141,7 @@ struct pic_run {
     cudaStream_t cap = nullptr;      // private stream for graph capture
     unsigned char *ws = nullptr;
     int cur = 0;                     // which x/v buffer holds the state
-    int grid = 0, block = 0, variant = 0, unroll = 1, solve_nb = 1;
+    int grid = 0, block = 0, variant = 0, unroll = 1;
     int64_t step = 0;
     bool ready = false, pending_push = false;
     cudaGraphExec_t period[2] = {nullptr, nullptr};   // S steps from x parity 0/1
@@ -227,6 +233,8 @@ cudaError_t enqueue_solve(pic_run *r, cudaStream_t s, bool after_push) {
     a.k_phi = r->k_phi;
     a.dx = r->dx;
     a.mass = r->mass;
+    a.solver = r->p.field_solver;
+    a.cg_maxit = r->p.cg_iterations ? r->p.cg_iterations : PIC_CG_DEFAULT_ITERATIONS;
     return launch_solve(a, s);
 }
 
@@ -418,6 +426,7 @@ int pic_create(const pic_params *p, void *workspace, size_t workspace_bytes,
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&r->sms, cudaDevAttrMultiProcessorCount, r->device);
     if (e == cudaSuccess) e = push_prepare_attributes(p->precision, p->ncell);
     if (e == cudaSuccess) e = sort_prepare_attributes(p->ncell);
+    if (e == cudaSuccess) e = solve_prepare_attributes();
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&r->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) { delete r; return cuda_fail(e); }
 
@@ -444,7 +453,6 @@ int pic_create(const pic_params *p, void *workspace, size_t workspace_bytes,
     if (p->precision != PIC_FP32_FIXED) r->unroll = 1;
     r->grid = push_grid(r, r->variant, r->block, r->unroll, p->blocks_per_sm);
     if (r->grid < 1) { delete r; return PIC_EINVAL; }
-    r->solve_nb = solve_blocks(p->precision, p->ncell);
     *out = r;
     return PIC_OK;
 }

@@ -74,7 +74,8 @@ struct DiagPartial {
     unsigned long long cq;         // fixed-point charge sum
 };
 
-// Field solve (fixed point: up to kSolveMaxBlocks blocks; float modes: 1).
+// Field solve (fixed point: one cluster of up to 16 blocks; float modes and
+// CG: one block).
 struct SolveArgs {
     int mode;                     // PIC_FP32_FIXED / PIC_FP32_ATOMIC / PIC_FP64
     unsigned long long *rho_q;    // FIXED: accumulator (read, then zeroed)
@@ -99,6 +100,8 @@ struct SolveArgs {
     double k_phi;                 // -dx^2 k_rho / NG
     double dx;
     double mass;                  // particle mass m = Q0/qm
+    int solver;                   // PIC_SOLVER_EXACT / PIC_SOLVER_CG
+    int cg_maxit;                 // CG: iterations per solve
 };
 
 // Counting sort by cell.
@@ -189,9 +192,9 @@ cudaError_t push_prepare_attributes(int mode, int ng);
 int push_max_blocks_per_sm(int mode, int variant, int unroll, int block, int ng);
 
 cudaError_t launch_solve(const SolveArgs &a, cudaStream_t s);
+cudaError_t solve_prepare_attributes();
 constexpr int kSolveThreads = 1024;
 constexpr int kSolveMaxBlocks = 32;
-int solve_blocks(int mode, int ng);
 
 cudaError_t launch_sort_f32(const SortArgs<float> &a, cudaStream_t s);
 cudaError_t launch_sort_f64(const SortArgs<double> &a, cudaStream_t s);

@@ -42,16 +42,26 @@ def test_phase_space_counts(nx, nv):
 
 
 def test_two_stream_beams_mix_by_t20():
-    # Fig. 1: at t = 0 two lines at v = +-0.2; at t = 20 vortices, with beam
-    # particles near v = 0 or moving the other way.
-    n = 20000
+    # Fig. 1: at t = 0 two lines at v = +-0.2; by t = 20 the instability has
+    # moved beam particles to velocities near zero.  The slow fraction is a
+    # coarse phase-space statistic, so it is compared with the oracle's run
+    # from the same state (8.9% of the particles at |v| < 0.1 at step 200).
+    import oracle as O
+    n, ng = 20000, 64
     x, v = W.two_stream(n, L4PI, 0.2, 0.01, 11)
-    run = pic.Run(pic.Params(npart=n, ncell=64, length=L4PI), device="cuda:0")
-    run.init(*W.to_f32_state(x, v, L4PI))
+    x32, v32 = W.to_f32_state(x, v, L4PI)
+    run = pic.Run(pic.Params(npart=n, ncell=ng, length=L4PI), device="cuda:0")
+    run.init(x32, v32)
     f0 = run.phase_space(64, 40, -0.4, 0.4)
     run.step_n(200)
     f20 = run.phase_space(64, 40, -0.4, 0.4)
     slow = slice(15, 25)                       # |v| < 0.1
     assert f0[slow].sum() == 0
-    assert f20[slow].sum() > 0.2 * n
     assert f0.sum() == n and f20.sum() <= n
+    st = O.State(O.params(ng, n, L4PI, 0.1), x32.astype(np.float64), v32.astype(np.float64))
+    for _ in range(200):
+        st.step()
+    frac_oracle = float(np.mean(np.abs(st.v) < 0.1))
+    frac_gpu = f20[slow].sum() / n
+    assert frac_oracle > 0.05
+    assert abs(frac_gpu - frac_oracle) < 0.01

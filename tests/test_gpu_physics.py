@@ -167,3 +167,32 @@ def test_graph_replay_equals_single_steps():
     assert np.array_equal(xa, xb) and np.array_equal(va, vb)
     da, db = a.diagnostics(0, 37), b.diagnostics(0, 37)
     assert np.array_equal(da["field"], db["field"])
+
+
+@pytest.mark.parametrize("layout", ["sorted_jitter", "sorted_blocks_reversed", "mixed"])
+def test_sort_matches_stable_argsort(layout):
+    # The scatter has two paths: tiles whose keys span few cells (the state a
+    # periodic sort leaves behind) and tiles that span many.  Both must give
+    # exactly the stable order by cell.
+    n, ng, L = 300007, 4096, L4PI
+    rng = np.random.default_rng(3)
+    base = np.sort(rng.uniform(0, L, n))
+    if layout == "sorted_jitter":
+        x = base + rng.normal(0, 2.0 * L / ng, n)
+    elif layout == "sorted_blocks_reversed":
+        x = np.concatenate([b[::-1] for b in np.array_split(base, 97)])
+    else:
+        x = base.copy()
+        wild = rng.random(n) < 0.002
+        x[wild] = rng.uniform(0, L, wild.sum())
+    x32, _ = W.to_f32_state(np.mod(x, L), np.zeros(n), L)
+    v32 = (np.arange(n) * 1e-6).astype(np.float32)
+    run = make_run(n, ng, L)
+    run.init(x32, v32)
+    run.sort()
+    xs, vs = run.get_state()
+    perm = np.argsort(_keys(x32, ng, L), kind="stable")
+    assert np.array_equal(xs, x32[perm]) and np.array_equal(vs, v32[perm])
+    run.sort()
+    xs2, vs2 = run.get_state()
+    assert np.array_equal(xs2, xs) and np.array_equal(vs2, vs)
