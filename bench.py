@@ -250,11 +250,12 @@ def time_ours(args, w, x32, v32):
     total_ms = t0.elapsed_time(t1)
     push_ms = [a.elapsed_time(b) for a, b in evs]
     run.sync()
-    grid, block, variant = run.launch_shape()
-    unroll = run.p.unroll
+    grid, block, variant, unroll = run.launch_shape()
     diag = run.diagnostics(run.step - 1, 1)[0]
     res = dict(total_ms=total_ms, push_ms=push_ms, clocks=ck, launches=launches["n"],
-               grid=grid, block=block, variant=variant, steps=K,
+               grid=grid, block=block, variant=variant, unroll=unroll,
+               blocks_per_sm=grid // max(1, torch.cuda.get_device_properties(0).multi_processor_count),
+               steps=K,
                energy=float(diag["kinetic"] + diag["field"]))
     run.close()
     return res
@@ -738,7 +739,8 @@ def main():
                    "precision": "f32 push, int64 fixed-point deposit, f64 field solve",
                    "l2": "inputs larger than L2 (%.0f MiB particle state)" % (16 * n / 2**20 / 2),
                    "launch": {"grid": res["grid"], "block": res["block"],
-                              "deposit_variant": res["variant"]}},
+                              "deposit_variant": res["variant"], "unroll": res["unroll"],
+                              "blocks_per_sm": res["blocks_per_sm"]}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": recorded_traffic(),
                      "kernel": "pic_push_fixed_kernel", "peak_source": src,

@@ -81,6 +81,16 @@ extern "C" {
  *          conjugate gradient from Phi = 0, a fixed number of iterations
  *          (the paper forces 150), float64, unconverged field included.
  *          Single runs only (the pool rejects it with PIC_EINVAL). */
+/* Particle shapes (pic_params.shape): how charge goes to the grid and the
+ * field comes back (Sec. 2.3 and Sec. 2), nodes at the cell centres.
+ *   CIC  the two-cell linear weighting of Sec. 2.3 and the listing (default);
+ *   NGP  nearest grid point: the cell the particle belongs to, floor(x NG/L)
+ *        in float32, takes its whole charge and gives its field (Sec. 2's
+ *        "counting the particles of a cell").  PIC_FP32_FIXED only; single
+ *        runs only (the pool rejects it). */
+#define PIC_SHAPE_CIC 0
+#define PIC_SHAPE_NGP 1
+
 #define PIC_SOLVER_EXACT 0
 #define PIC_SOLVER_CG 1
 #define PIC_CG_DEFAULT_ITERATIONS 150
@@ -109,6 +119,8 @@ typedef struct pic_params {
     int32_t cg_iterations; /* PIC_SOLVER_CG: iterations per solve, run to the
                               end whether converged or not (0 = 150, the
                               paper's fixed count; at most 100000)           */
+    int32_t shape;         /* PIC_SHAPE_CIC | PIC_SHAPE_NGP                    */
+    int32_t reserved;      /* must be 0                                       */
 } pic_params;
 
 /* One row of the per-step diagnostics (all float64 on the device). */
@@ -152,7 +164,9 @@ void pic_destroy(pic_run *run);
  * (float for the FP32 modes, double for PIC_FP64); v0 is v^{-1/2}.  Positions
  * must lie in [0, L).  Copies them to the device, deposits rho^0, solves Phi^0
  * and E^0 and resets the step counter to 0.  Synchronises the stream (the host
- * arrays may be reused on return).  PIC_EINVAL for positions outside [0, L). */
+ * arrays may be reused on return).  PIC_EINVAL for positions outside [0, L)
+ * (checked on the device after the upload; the run then holds no usable
+ * state, and calls other than pic_init / pic_set_state return PIC_ESTATE). */
 int pic_init(pic_run *run, const void *x0, const void *v0);
 
 /* Charge deposit (Sec. 2.3) of the current positions into the density
@@ -242,9 +256,11 @@ int pic_phase_space(pic_run *run, int32_t nx, int32_t nv, double vmin, double vm
  * sort) and of the float32 field used by the gather. */
 int pic_device_arrays(pic_run *run, void **x, void **v, void **E32);
 
-/* The launch shape the run uses for its fused push. */
+/* The launch shape the run uses for its fused push (any pointer may be
+ * NULL): grid, threads per block, deposit variant (6: the NGP shape's
+ * kernel), float4 groups per thread per iteration. */
 int pic_launch_shape(const pic_run *run, int32_t *grid, int32_t *block,
-                     int32_t *variant);
+                     int32_t *variant, int32_t *unroll);
 
 /* Device-side initial loading of a two-stream plasma (Sec. 2 "initialization",
  * the Appendix A set-up, the Sec. 4 beams).  Particle j of N:

@@ -42,13 +42,18 @@ def build(force: bool = False) -> str:
 
 class Params(C.Structure):
     """orc_params: the Appendix A parameter block."""
-    _fields_ = [("ng", C.c_int32), ("pad_", C.c_int32), ("np", C.c_int64),
+    _fields_ = [("ng", C.c_int32), ("shape", C.c_int32), ("np", C.c_int64),
                 ("lx", C.c_double), ("dt", C.c_double),
                 ("qoms0", C.c_double), ("rho_init0", C.c_double)]
 
 
-def params(ng, np_, lx, dt=0.1, qoms0=-1.0, rho_init0=1.0) -> Params:
-    return Params(int(ng), 0, int(np_), float(lx), float(dt), float(qoms0),
+CIC, NGP = 0, 1
+
+
+def params(ng, np_, lx, dt=0.1, qoms0=-1.0, rho_init0=1.0, shape=CIC) -> Params:
+    """shape: CIC (the listing's two-cell weighting) or NGP (nearest grid
+    point: the particle's own cell)."""
+    return Params(int(ng), int(shape), int(np_), float(lx), float(dt), float(qoms0),
                   float(rho_init0))
 
 
@@ -84,6 +89,8 @@ def _load():
                 "orc_mode_amplitudes": (None, [_P, _D, C.c_int, _D]),
                 "orc_deposit_fixed": (C.c_int, [C.c_int32, C.c_double,
                                                 C.c_int64, _F, _L]),
+                "orc_deposit_fixed_ngp": (C.c_int, [C.c_int32, C.c_double,
+                                                    C.c_int64, _F, _L]),
                 "orc_rho_from_fixed": (None, [_P, _L, _D]),
                 "orc_fix_bits": (C.c_int, []),
             }
@@ -246,6 +253,17 @@ def deposit_fixed(ng: int, lx: float, x32) -> np.ndarray:
                                      x32.ctypes.data_as(_F),
                                      rho_q.ctypes.data_as(_L)),
            "fixed deposit")
+    return rho_q
+
+
+def deposit_fixed_ngp(ng: int, lx: float, x32) -> np.ndarray:
+    """Fixed-point nearest-grid-point deposit of float32 positions (R13)."""
+    x32 = np.ascontiguousarray(x32, dtype=np.float32)
+    rho_q = np.zeros(int(ng), dtype=np.int64)
+    _check(_load().orc_deposit_fixed_ngp(int(ng), float(lx), x32.size,
+                                         x32.ctypes.data_as(_F),
+                                         rho_q.ctypes.data_as(_L)),
+           "fixed NGP deposit")
     return rho_q
 
 

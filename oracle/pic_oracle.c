@@ -25,7 +25,9 @@
  *       garbled "w1 = (x_p - x_g)/dx" sentence of Sec. 2.3;
  *   R3  wrap: positions live in [0, Lx);
  *   R5  fixed-point deposit (orc_deposit_fixed): the build's exact integer
- *       form of the Sec. 2.3 weighting, stated at the function.
+ *       form of the Sec. 2.3 weighting, stated at the function;
+ *   R13 nearest-grid-point weighting (shape ORC_NGP): the cell xp belongs
+ *       to, trunc(xp/dx), takes the whole charge and gives its field.
  *
  * Parity status: every exported function is pinned by a test against
  * something other than itself (closed forms, invariants, brute force, a
@@ -42,7 +44,8 @@
 /* Run parameters, named as in the Appendix A parameter block. */
 typedef struct orc_params {
     int32_t ng;        /* NG: number of cells (grid points)              */
-    int32_t pad_;
+    int32_t shape;     /* ORC_CIC (the listing's two-cell weighting) or
+                          ORC_NGP (the cell's own node, Sec. 2)          */
     int64_t np;        /* NP: number of particles                        */
     double  lx;        /* Lx: box length                                 */
     double  dt;        /* dt: time step                                  */
@@ -53,6 +56,9 @@ typedef struct orc_params {
 #define ORC_OK 0
 #define ORC_EINVAL (-1)
 #define ORC_ERANGE (-2)
+
+#define ORC_CIC 0
+#define ORC_NGP 1
 
 static double orc_dx(const orc_params *p) { return p->lx / (double)p->ng; }
 
@@ -92,8 +98,33 @@ static double orc_wrap(double x, double lx)
  * periodically (ig = 0 shares with node NG-1, ig = NG is node 0), which is
  * what the listing's ghost cells do with a single domain.
  * Returns ORC_ERANGE if a position lies outside [0, Lx]. */
+/* Nearest-grid-point weighting (Sec. 2: the density at a grid point counts
+ * the particles of its cell, and a particle feels the field of the cell it
+ * belongs to).  With nodes at the cell centres, the cell of xp is
+ * ig = trunc(xp/dx) and its node is the nearest one; xp == Lx is the periodic
+ * image of 0 (cell 0). */
+static int orc_cell_ngp(const orc_params *p, double x)
+{
+    int ig = (int)(x / orc_dx(p));
+    return ig >= p->ng ? ig - p->ng : ig;
+}
+
+static int orc_deposit_ngp(const orc_params *p, const double *xp, double *rho)
+{
+    const int ng = p->ng;
+    const double dx = orc_dx(p), Q0 = orc_q0(p);
+    for (int ic = 0; ic < ng; ic++) rho[ic] = p->rho_init0;
+    for (int64_t ip = 0; ip < p->np; ip++) {
+        double x = xp[ip];
+        if (!(x >= 0.0 && x <= p->lx)) return ORC_ERANGE;
+        rho[orc_cell_ngp(p, x)] += Q0 / dx;
+    }
+    return ORC_OK;
+}
+
 int orc_deposit(const orc_params *p, const double *xp, double *rho)
 {
+    if (p->shape == ORC_NGP) return orc_deposit_ngp(p, xp, rho);
     const int ng = p->ng;
     const double dx = orc_dx(p), Q0 = orc_q0(p);
     const double xg_last = dx / 2.0 + dx * (ng - 1);
@@ -208,6 +239,14 @@ void orc_efield(const orc_params *p, const double *phi, double *E)
 int orc_gather(const orc_params *p, const double *xp, const double *E,
                double *Ex)
 {
+    if (p->shape == ORC_NGP) {
+        for (int64_t ip = 0; ip < p->np; ip++) {
+            double x = xp[ip];
+            if (!(x >= 0.0 && x <= p->lx)) return ORC_ERANGE;
+            Ex[ip] = E[orc_cell_ngp(p, x)];
+        }
+        return ORC_OK;
+    }
     const int ng = p->ng;
     const double dx = orc_dx(p);
     const double xg_last = dx / 2.0 + dx * (ng - 1);
@@ -394,6 +433,26 @@ int orc_deposit_fixed(int32_t ng, double lx, int64_t np, const float *x,
         int ir = (il + 1 == ng) ? 0 : il + 1;
         rho_q[ir] += (int64_t)W;
         rho_q[il] += (int64_t)((1u << ORC_FIX_BITS) - W);
+    }
+    return ORC_OK;
+}
+
+/* The fixed-point form of the nearest-grid-point weighting (reading R13):
+ *   u = x * c  (one float multiplication, round to nearest),
+ *   i = (int)floorf(u), cell NG (x rounding up to the box end) is cell 0,
+ *   rho_q[i] += 2^24. */
+int orc_deposit_fixed_ngp(int32_t ng, double lx, int64_t np, const float *x,
+                          int64_t *rho_q)
+{
+    const float c = (float)((double)ng / lx);
+    for (int g = 0; g < ng; g++) rho_q[g] = 0;
+    for (int64_t ip = 0; ip < np; ip++) {
+        float u = x[ip] * c;
+        float fl = floorf(u);
+        if (!(fl >= 0.0f && fl <= (float)ng)) return ORC_ERANGE;
+        int i = (int)fl;
+        if (i == ng) i = 0;
+        rho_q[i] += (int64_t)1 << ORC_FIX_BITS;
     }
     return ORC_OK;
 }

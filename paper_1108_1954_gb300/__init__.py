@@ -32,6 +32,7 @@ PIC_FP32_FIXED, PIC_FP32_ATOMIC, PIC_FP64 = 0, 1, 2
 PIC_DEPOSIT_AUTO, PIC_DEPOSIT_ATOMIC, PIC_DEPOSIT_MATCH = 0, 1, 2
 PIC_DEPOSIT_PACKED, PIC_DEPOSIT_MATCH_PACKED, PIC_DEPOSIT_QUAD = 3, 4, 5
 PIC_SOLVER_EXACT, PIC_SOLVER_CG = 0, 1
+PIC_SHAPE_CIC, PIC_SHAPE_NGP = 0, 1
 PIC_CG_DEFAULT_ITERATIONS = 150
 PIC_NCELL_MAX = 8192
 PIC_NMODES = 8
@@ -51,7 +52,8 @@ class CParams(C.Structure):
                 ("history", C.c_int32), ("deposit_variant", C.c_int32),
                 ("block_size", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("unroll", C.c_int32), ("field_solver", C.c_int32),
-                ("cg_iterations", C.c_int32)]
+                ("cg_iterations", C.c_int32), ("shape", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class CDiagRow(C.Structure):
@@ -92,7 +94,7 @@ _SIG = {
     "pic_get_field": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "pic_device_arrays": (C.c_int, [_VP, C.POINTER(_VP), C.POINTER(_VP),
                                     C.POINTER(_VP)]),
-    "pic_launch_shape": (C.c_int, [_VP, C.POINTER(C.c_int32),
+    "pic_launch_shape": (C.c_int, [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "pic_autotune": (C.c_int, [_VP, C.c_int32, _VP, C.c_int32, C.POINTER(C.c_int32)]),
     "pic_set_launch": (C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
@@ -165,6 +167,7 @@ class Params:
     unroll: int = 0
     field_solver: int = 0          # PIC_SOLVER_EXACT
     cg_iterations: int = 0         # 0: the paper's 150
+    shape: int = 0                 # PIC_SHAPE_CIC
 
     def c(self) -> CParams:
         return CParams(int(self.npart), int(self.ncell), int(self.precision),
@@ -173,7 +176,7 @@ class Params:
                        int(self.history), int(self.deposit_variant),
                        int(self.block_size), int(self.blocks_per_sm),
                        int(self.unroll), int(self.field_solver),
-                       int(self.cg_iterations))
+                       int(self.cg_iterations), int(self.shape), 0)
 
     @property
     def dtype(self):
@@ -321,10 +324,11 @@ class Run:
         return out[:n.value]
 
     def launch_shape(self):
-        g, b, v = C.c_int32(), C.c_int32(), C.c_int32()
-        _check(_lib.pic_launch_shape(self._h, C.byref(g), C.byref(b), C.byref(v)),
+        """(grid, block, variant, unroll) of the fused push."""
+        g, b, v, u = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        _check(_lib.pic_launch_shape(self._h, C.byref(g), C.byref(b), C.byref(v), C.byref(u)),
                "pic_launch_shape")
-        return int(g.value), int(b.value), int(v.value)
+        return int(g.value), int(b.value), int(v.value), int(u.value)
 
 
 PIC_LOAD_MAX_MODES = 8

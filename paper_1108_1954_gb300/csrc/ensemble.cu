@@ -338,7 +338,7 @@ int check_admit(const pic_pool *pool, const pic_params *p) {
     int rc = validate_params(p);
     if (rc) return rc;
     if (p->precision != PIC_FP32_FIXED || p->ncell > pool->cfg.ncell_max) return PIC_EINVAL;
-    if (p->field_solver != PIC_SOLVER_EXACT) return PIC_EINVAL;
+    if (p->field_solver != PIC_SOLVER_EXACT || p->shape != PIC_SHAPE_CIC) return PIC_EINVAL;
     return PIC_OK;
 }
 

@@ -46,7 +46,10 @@ namespace cg = cooperative_groups;
 namespace pic {
 namespace {
 
-constexpr int kClusterSolveThreads = 512;   // nodes per block (one per thread)
+constexpr int kClusterSolveThreads = 512;   // most nodes per block (one per thread)
+// nodes per block of the exact solve: its per-node float64 conversions and
+// diagnostics are the critical path, so spread them over up to 16 SMs
+constexpr int kSolveNodesPerBlock = 256;
 constexpr int kMaxSolveCluster = 16;        // blocks per cluster (16: non-portable)
 
 // The block's share of the diagnostics, written to a.dpart[blockIdx.x]; the
@@ -192,17 +195,24 @@ struct ClusterDiag {
     unsigned long long cq;        // slice sum of rho_q
 };
 
-// The block's share of the push's per-block sums (summed over the block;
-// valid in warp 0).  Issued first in the solves, so the loads overlap.
-__device__ __forceinline__ void push_sums_share(const SolveArgs &a, int C, int r, double (&kv)[2],
-                                                double *shd) {
+// The block's share of the push's per-block sums, summed by warp 0 alone
+// (a few dozen values; float64 adds are scarce); valid in lane 0 of warp 0.
+// Issued first in the solves, so the loads overlap the rest.
+__device__ __forceinline__ void push_sums_share(const SolveArgs &a, int C, int r, double (&kv)[2]) {
     kv[0] = 0.0;
     kv[1] = 0.0;
-    for (int i = r * blockDim.x + threadIdx.x; i < a.npartials; i += C * blockDim.x) {
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    for (int i = r * 32 + lane; i < a.npartials; i += C * 32) {
         kv[0] += a.partials[2 * i];
         kv[1] += a.partials[2 * i + 1];
     }
-    block_sum_t<2, double>(kv, shd);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double u0 = __shfl_down_sync(kFull, kv[0], o);
+        const double u1 = __shfl_down_sync(kFull, kv[1], o);
+        if (lane < o) { kv[0] += u0; kv[1] += u1; }
+    }
 }
 
 // Diagnostics of a cluster solve: block sums of the nodes' contributions,
@@ -218,8 +228,7 @@ __device__ void cluster_finish(const SolveArgs &a, cg::cluster_group &cl, Cluste
     __shared__ unsigned long long cqw[32];
     const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
     const int T = blockDim.x, t = threadIdx.x, lane = t & 31;
-    double dv[1] = {d.fe};
-    block_sum_t<1, double>(dv, shd);
+    const double fe = block_sum_f64(d.fe, shd);
     float md[2 * PIC_NMODES];
 #pragma unroll
     for (int m = 0; m < PIC_NMODES; m++) { md[2 * m] = d.re[m]; md[2 * m + 1] = d.im[m]; }
@@ -240,7 +249,7 @@ __device__ void cluster_finish(const SolveArgs &a, cg::cluster_group &cl, Cluste
             cd.cq = s;
             cd.kv[0] = kv[0];
             cd.kv[1] = kv[1];
-            cd.diag[kDiagFE] = dv[0];
+            cd.diag[kDiagFE] = fe;
             cd.diag[kDiagKE] = 0.0;
             cd.diag[kDiagMom] = 0.0;
             cd.diag[kDiagCharge] = charge;
@@ -316,7 +325,6 @@ __global__ void __launch_bounds__(kClusterSolveThreads) pic_solve_cluster_kernel
     __shared__ i128 sh[96];
     __shared__ i128 wlast[32];
     __shared__ i128 pre[4];
-    __shared__ double shd[32 * 2];
     const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
     const int ng = a.ng, t = threadIdx.x, lane = t & 31;
     const long long step = *a.dstep;
@@ -333,7 +341,7 @@ __global__ void __launch_bounds__(kClusterSolveThreads) pic_solve_cluster_kernel
         a.rho_q_last[g] = q;
     }
     double kv[2];
-    push_sums_share(a, C, r, kv, shd);
+    push_sums_share(a, C, r, kv);
     const i128 R = mine ? (i128)ntot - (i128)ng * (i128)q : (i128)0;
     {
         i128 S0 = R, S1 = R * (i128)g, Sz = 0;
@@ -435,7 +443,6 @@ __global__ void __launch_bounds__(kClusterSolveThreads) pic_solve_cg_kernel(Solv
     __shared__ CgExchange ex;
     __shared__ ClusterDiag cd;
     __shared__ double slot[32];
-    __shared__ double shd[32 * 2];
     __shared__ i128 sh[96];
     const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
     const int ng = a.ng, t = threadIdx.x;
@@ -447,7 +454,7 @@ __global__ void __launch_bounds__(kClusterSolveThreads) pic_solve_cg_kernel(Solv
     const int g = b0 + t;
     const bool mine = t < cnt;
     double kv[2];
-    push_sums_share(a, C, r, kv, shd);
+    push_sums_share(a, C, r, kv);
     double rh = 0.0;
     unsigned long long q = 0ull;
     i128 R = 0;
@@ -667,7 +674,7 @@ __global__ void __launch_bounds__(kSolveThreads) pic_solve_float_kernel(SolveArg
 
 // Cluster shape of the solves: C = ceil(NG / per_block) blocks (at most 16),
 // ceil(NG / C) nodes each, rounded up to whole warps.  The exact solve takes
-// up to 512 nodes per block, the CG 32 (its iterations are float64-bound).
+// up to 256 nodes per block, the CG 32 (both are float64-bound on GB300).
 void solve_cluster_shape(int ng, int per_block, int *C, int *threads) {
     int c = (ng + per_block - 1) / per_block;
     c = c < 1 ? 1 : (c > kMaxSolveCluster ? kMaxSolveCluster : c);
@@ -687,7 +694,7 @@ cudaError_t solve_prepare_attributes() {
 cudaError_t launch_solve(const SolveArgs &a, cudaStream_t s) {
     if (a.solver == PIC_SOLVER_CG || a.mode == PIC_FP32_FIXED) {
         int C = 1, threads = 32;
-        solve_cluster_shape(a.ng, a.solver == PIC_SOLVER_CG ? 32 : kClusterSolveThreads, &C,
+        solve_cluster_shape(a.ng, a.solver == PIC_SOLVER_CG ? 32 : kSolveNodesPerBlock, &C,
                             &threads);
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];

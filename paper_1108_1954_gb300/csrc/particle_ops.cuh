@@ -51,6 +51,21 @@ __device__ __forceinline__ unsigned fixed_weight(float f) {
     return __float2uint_rz(__fmul_rn(f, 16777216.0f));
 }
 
+// Kick (Eq. 3), drift (Eq. 2) and wrap of one particle, given the field ep
+// at the particle; accumulates v_old v_new and v_new.
+__device__ __forceinline__ void kick_drift_wrap(float &x, float &v, float ep, const PushConsts &c,
+                                                float &ke, float &mom) {
+    const float vn = fmaf(c.qmdt, ep, v);
+    ke = fmaf(v, vn, ke);
+    mom += vn;
+    float xn = fmaf(vn, c.dt, x);
+    xn = xn < 0.0f ? xn + c.length : xn;
+    xn = xn >= c.length ? xn - c.length : xn;
+    xn = xn >= c.length ? 0.0f : xn;   // x + L rounded up to L: the point 0
+    x = xn;
+    v = vn;
+}
+
 // Gather (left and right node), kick, drift, wrap.
 // sE[j] = E_{(j-1) mod NG} for j = 0..NG+1 (ghost-padded).
 __device__ __forceinline__ void push_particle(float &x, float &v, const float *sE,
@@ -61,15 +76,28 @@ __device__ __forceinline__ void push_particle(float &x, float &v, const float *s
     const unsigned j = ok ? l.j : 0u;
     const float e0 = sE[j], e1 = sE[j + 1];
     const float ep = ok ? fmaf(l.f, e1 - e0, e0) : 0.0f;
-    const float vn = fmaf(c.qmdt, ep, v);
-    ke = fmaf(v, vn, ke);
-    mom += vn;
-    float xn = fmaf(vn, c.dt, x);
-    xn = xn < 0.0f ? xn + c.length : xn;
-    xn = xn >= c.length ? xn - c.length : xn;
-    xn = xn >= c.length ? 0.0f : xn;   // x + L rounded up to L: the point 0
-    x = xn;
-    v = vn;
+    kick_drift_wrap(x, v, ep, c, ke, mom);
+}
+
+// Nearest-grid-point weighting (PIC_SHAPE_NGP; Sec. 2: a grid point's density
+// counts the particles of its cell, and a particle feels its cell's field):
+// with nodes at the cell centres the cell of x is floor(x * c), formed by the
+// same rounded-down magic sum as locate (exact on [-1, 8193]).  Returns the
+// ghost-padded tile index j = cell + 1 (cell NG, a position rounding up to
+// the box end, is j = NG + 1, the ghost of node 0); a valid position has
+// j - 1 in [0, NG] (one unsigned test).
+__device__ __forceinline__ unsigned locate_ngp(float x, float inv_dx) {
+    const float t = __fadd_rd(__fmul_rn(x, inv_dx), kMagic);
+    return (unsigned)(__float_as_int(t) - kMagicBitsMinus1);
+}
+
+__device__ __forceinline__ void push_particle_ngp(float &x, float &v, const float *sE,
+                                                  const PushConsts &c, float &ke,
+                                                  float &mom) {
+    const unsigned j = locate_ngp(x, c.inv_dx);
+    const bool ok = j - 1u <= (unsigned)c.ng;
+    const float ep = ok ? sE[j] : 0.0f;
+    kick_drift_wrap(x, v, ep, c, ke, mom);
 }
 
 // Shared-memory density tiles.  GB300 has no single-instruction 64-bit
@@ -95,6 +123,13 @@ __device__ __forceinline__ void tile_add(const Tile &t, unsigned j, unsigned val
 template <int VARIANT>
 __device__ __forceinline__ void deposit_one(const Tile &t, float x, bool valid,
                                             const PushConsts &c, unsigned *err, int lane) {
+    if (VARIANT == kDepositNgp) {
+        const unsigned j = locate_ngp(x, c.inv_dx);
+        const bool ok = valid && j - 1u <= (unsigned)c.ng;
+        if (valid && !ok) atomicOr(err, kErrPosition);
+        if (ok) tile_add(t, j, kFixOne);
+        return;
+    }
     const Loc l = locate(x, c.inv_dx);
     const bool ok = valid && l.j <= (unsigned)c.ng;
     if (valid && !ok) atomicOr(err, kErrPosition);
@@ -128,7 +163,26 @@ template <int VARIANT>
 __device__ __forceinline__ void deposit4(const Tile &t, const float4 &xx, bool valid,
                                          const PushConsts &c, unsigned *err, int lane) {
     const float xs[4] = {xx.x, xx.y, xx.z, xx.w};
-    if (VARIANT == PIC_DEPOSIT_QUAD) {
+    if (VARIANT == kDepositNgp) {
+        // runs of equal cell among the 4 particles: count * 2^24 per run
+        unsigned key = 0xffffffffu, cnt = 0;
+        bool bad = false;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const unsigned j = locate_ngp(xs[k], c.inv_dx);
+            const bool ok = valid && j - 1u <= (unsigned)c.ng;
+            bad |= valid && !ok;
+            if (ok && j == key) {
+                cnt += kFixOne;
+            } else if (ok) {
+                if (key != 0xffffffffu) tile_add(t, key, cnt);
+                key = j;
+                cnt = kFixOne;
+            }
+        }
+        if (key != 0xffffffffu) tile_add(t, key, cnt);
+        if (bad) atomicOr(err, kErrPosition);
+    } else if (VARIANT == PIC_DEPOSIT_QUAD) {
         // consecutive particles of the group with equal left node are summed
         // in registers first (at most 4 * 2^24 per word), then added once
         unsigned key = 0xffffffffu, left = 0, right = 0;

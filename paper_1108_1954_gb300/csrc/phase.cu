@@ -1,5 +1,6 @@
 // phase.cu -- phase-space histogram f(x, v) of the particles (the (x, v)
-// snapshots of the Sec. 4 verification test, Fig. 1), on the device.
+// snapshots of the Sec. 4 verification test, Fig. 1), on the device; and the
+// range check of uploaded positions.
 //
 // Bin rule (float32, as stated in include/pic.h): ix = min(nx - 1,
 // trunc(x * (nx / L))), iv = floor((v - vmin) * (nv / (vmax - vmin))); a
@@ -50,5 +51,35 @@ cudaError_t launch_phase(const PhaseArgs<T> &a, int sms, cudaStream_t s) {
 
 template cudaError_t launch_phase<float>(const PhaseArgs<float> &, int, cudaStream_t);
 template cudaError_t launch_phase<double>(const PhaseArgs<double> &, int, cudaStream_t);
+
+// Uploaded positions must lie in [0, L) (NaN fails); one flag per block.
+namespace {
+template <typename T>
+__global__ void __launch_bounds__(256) check_positions_kernel(const T *x, long long n, T length,
+                                                              unsigned *err) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    bool bad = false;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const T xi = __ldcs(x + i);
+        bad |= !(xi >= (T)0 && xi < length);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, kErrInput);
+}
+}  // namespace
+
+template <typename T>
+cudaError_t launch_check_positions(const T *x, long long n, T length, unsigned *err, int sms,
+                                   cudaStream_t s) {
+    long long blocks = (n + 255) / 256;
+    if (blocks > (long long)sms * 8) blocks = (long long)sms * 8;
+    if (blocks < 1) blocks = 1;
+    check_positions_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(x, n, length, err);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_check_positions<float>(const float *, long long, float, unsigned *, int,
+                                                   cudaStream_t);
+template cudaError_t launch_check_positions<double>(const double *, long long, double, unsigned *,
+                                                    int, cudaStream_t);
 
 }  // namespace pic

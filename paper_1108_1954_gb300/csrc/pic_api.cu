@@ -45,6 +45,9 @@ int pic::validate_params(const pic_params *p) {
     if (p->unroll != 0 && p->unroll != 1 && p->unroll != 2 && p->unroll != 4) return PIC_EINVAL;
     if (p->field_solver != PIC_SOLVER_EXACT && p->field_solver != PIC_SOLVER_CG) return PIC_EINVAL;
     if (p->cg_iterations < 0 || p->cg_iterations > 100000) return PIC_EINVAL;
+    if (p->shape != PIC_SHAPE_CIC && p->shape != PIC_SHAPE_NGP) return PIC_EINVAL;
+    if (p->shape == PIC_SHAPE_NGP && p->precision != PIC_FP32_FIXED) return PIC_EINVAL;
+    if (p->reserved != 0) return PIC_EINVAL;
     return PIC_OK;
 }
 
@@ -326,34 +329,28 @@ int push_grid(const pic_run *r, int variant, int block, int unroll, int bps_cap)
     return (int)want;
 }
 
-int check_host_positions(const pic_run *r, const void *x) {
-    const int64_t n = r->p.npart;
-    if (r->p.precision == PIC_FP64) {
-        const double *xd = (const double *)x;
-        for (int64_t i = 0; i < n; i++)
-            if (!(xd[i] >= 0.0 && xd[i] < r->p.length)) return PIC_EINVAL;
-    } else {
-        const float *xf = (const float *)x;
-        const float L = r->pc.length;
-        for (int64_t i = 0; i < n; i++)
-            if (!(xf[i] >= 0.0f && xf[i] < L)) return PIC_EINVAL;
-    }
-    return PIC_OK;
-}
-
 int read_error_word(pic_run *r) {
     unsigned err = 0;
     PIC_CUDA(cudaMemcpyAsync(&err, &r->dev()->err, sizeof(err), cudaMemcpyDeviceToHost, r->stream));
     PIC_CUDA(cudaStreamSynchronize(r->stream));
     if (err & kErrTimeout) return PIC_ETIMEOUT;
+    if (err & kErrInput) return PIC_EINVAL;
     return err ? PIC_EDEVICE : PIC_OK;
 }
 
 // With x, v in buffer 0: reset the run, deposit and solve: E^step ready.
-int prepare_loaded(pic_run *r, int64_t step) {
+int prepare_loaded(pic_run *r, int64_t step, bool check) {
     DevScalars ds{};
     ds.step = step;
     PIC_CUDA(cudaMemcpyAsync(r->dev(), &ds, sizeof(ds), cudaMemcpyHostToDevice, r->stream));
+    if (check) {
+        if (r->p.precision == PIC_FP64)
+            PIC_CUDA(launch_check_positions((const double *)r->xs(0), r->p.npart, r->p.length,
+                                            &r->dev()->err, r->sms, r->stream));
+        else
+            PIC_CUDA(launch_check_positions((const float *)r->xs(0), r->p.npart, r->pc.length,
+                                            &r->dev()->err, r->sms, r->stream));
+    }
     PIC_CUDA(cudaMemsetAsync(r->ws + r->lay.rho_q, 0, (size_t)r->p.ncell * 8, r->stream));
     PIC_CUDA(cudaMemsetAsync(r->ws + r->lay.rho_f32, 0, (size_t)r->p.ncell * 4, r->stream));
     PIC_CUDA(cudaMemsetAsync(r->ws + r->lay.rho_f64, 0, (size_t)r->p.ncell * 8, r->stream));
@@ -362,21 +359,22 @@ int prepare_loaded(pic_run *r, int64_t step) {
     PIC_CUDA(enqueue_solve(r, r->stream, false));
     PIC_CUDA(cudaStreamSynchronize(r->stream));
     r->step = step;
-    r->ready = true;
     r->pending_push = false;
-    return read_error_word(r);
+    const int rc = read_error_word(r);
+    r->ready = rc == PIC_OK;       // a rejected upload leaves no usable state
+    return rc;
 }
 
 // Upload a state, deposit it and solve: E^step ready.
+// The positions are range-checked on the device after the upload (a host
+// loop over N positions cost more than the whole upload).
 int load_state(pic_run *r, const void *x, const void *v, int64_t step) {
     if (!x || !v) return PIC_EINVAL;
-    int rc = check_host_positions(r, x);
-    if (rc) return rc;
     const size_t bytes = (size_t)r->p.npart * r->elem();
     r->cur = 0;
     PIC_CUDA(cudaMemcpyAsync(r->xs(0), x, bytes, cudaMemcpyHostToDevice, r->stream));
     PIC_CUDA(cudaMemcpyAsync(r->vs(0), v, bytes, cudaMemcpyHostToDevice, r->stream));
-    return prepare_loaded(r, step);
+    return prepare_loaded(r, step, true);
 }
 
 }  // namespace
@@ -448,6 +446,7 @@ int pic_create(const pic_params *p, void *workspace, size_t workspace_bytes,
     // launch shape of the fused push
     r->variant = p->deposit_variant ? p->deposit_variant : PIC_DEPOSIT_QUAD;
     if (p->precision != PIC_FP32_FIXED) r->variant = PIC_DEPOSIT_ATOMIC;
+    if (p->shape == PIC_SHAPE_NGP) r->variant = kDepositNgp;
     r->block = p->block_size ? p->block_size : (p->precision == PIC_FP32_FIXED ? 512 : 256);
     r->unroll = p->unroll ? p->unroll : 1;
     if (p->precision != PIC_FP32_FIXED) r->unroll = 1;
@@ -478,7 +477,7 @@ int pic_init_loaded(pic_run *run, const pic_loading *ld) {
     if (rc) return rc;
     run->cur = 0;
     PIC_CUDA(launch_load(a, run->sms, run->stream));
-    return prepare_loaded(run, 0);
+    return prepare_loaded(run, 0, false);
 }
 
 int pic_set_state(pic_run *run, const void *x, const void *v, int64_t step) {
@@ -643,11 +642,13 @@ int pic_device_arrays(pic_run *run, void **x, void **v, void **E32) {
     return PIC_OK;
 }
 
-int pic_launch_shape(const pic_run *run, int32_t *grid, int32_t *block, int32_t *variant) {
+int pic_launch_shape(const pic_run *run, int32_t *grid, int32_t *block, int32_t *variant,
+                     int32_t *unroll) {
     if (!run) return PIC_EINVAL;
     if (grid) *grid = run->grid;
     if (block) *block = run->block;
     if (variant) *variant = run->variant;
+    if (unroll) *unroll = run->unroll;
     return PIC_OK;
 }
 
@@ -656,10 +657,12 @@ int pic_set_launch(pic_run *run, int32_t variant, int32_t block, int32_t unroll,
     if (!run) return PIC_EINVAL;
     if (run->pending_push) return PIC_ESTATE;
     const bool fixed = run->p.precision == PIC_FP32_FIXED;
+    const bool ngp = run->p.shape == PIC_SHAPE_NGP;
+    if (ngp && variant) return PIC_EINVAL;   // the shape fixes the deposit
     const int v = variant ? variant : run->variant;
     const int b = block ? block : run->block;
     const int u = unroll ? unroll : run->unroll;
-    if (v < PIC_DEPOSIT_ATOMIC || v > PIC_DEPOSIT_QUAD || (!fixed && v != PIC_DEPOSIT_ATOMIC))
+    if (!ngp && (v < PIC_DEPOSIT_ATOMIC || v > PIC_DEPOSIT_QUAD || (!fixed && v != PIC_DEPOSIT_ATOMIC)))
         return PIC_EINVAL;
     if (b < 32 || b % 32 || b > (fixed ? 512 : 1024)) return PIC_EINVAL;
     if ((u != 1 && u != 2 && u != 4) || (!fixed && u != 1)) return PIC_EINVAL;
@@ -682,6 +685,7 @@ int pic_autotune(pic_run *run, int32_t reps, pic_tune_entry *results,
     if (run->p.precision != PIC_FP32_FIXED) return PIC_OK;
     static const int variants[] = {PIC_DEPOSIT_ATOMIC, PIC_DEPOSIT_MATCH, PIC_DEPOSIT_PACKED,
                                    PIC_DEPOSIT_MATCH_PACKED, PIC_DEPOSIT_QUAD};
+    static const int ngp_only[] = {kDepositNgp};
     static const int blocks[] = {128, 256, 512};
     static const int unrolls[] = {1, 2};
     const size_t bytes = (size_t)run->p.npart * run->elem();
@@ -697,8 +701,12 @@ int pic_autotune(pic_run *run, int32_t reps, pic_tune_entry *results,
     // on a copy of the current order and on a freshly sorted copy, and the sum
     // is minimised.
     const int phases = run->p.sort_interval > 0 ? 2 : 1;
-    for (int v : variants)
-        for (int b : blocks)
+    const bool ngp = run->p.shape == PIC_SHAPE_NGP;
+    const int *vlist = ngp ? ngp_only : variants;
+    const int nv = ngp ? 1 : (int)(sizeof(variants) / sizeof(variants[0]));
+    for (int iv = 0; iv < nv; iv++)
+        for (int b : blocks) {
+            const int v = vlist[iv];
             for (int u : unrolls) {
                 const int g = push_grid(run, v, b, u, run->p.blocks_per_sm);
                 if (g < 1) continue;
@@ -743,6 +751,7 @@ int pic_autotune(pic_run *run, int32_t reps, pic_tune_entry *results,
                 count++;
                 if (med < best) { best = med; bv = v; bb = b; bu = u; bg = g; }
             }
+        }
     run->variant = bv;
     run->block = bb;
     run->unroll = bu;

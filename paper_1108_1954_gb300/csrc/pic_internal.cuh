@@ -21,6 +21,7 @@ enum : uint32_t {
     kErrPosition = 1u,   // a position outside [0, L) or not finite
     kErrTimeout = 2u,    // a bounded device wait ran out
     kErrSortKey = 4u,    // a sort key outside the grid
+    kErrInput = 8u,      // an uploaded position outside [0, L) (pic_init, pic_set_state)
 };
 
 // Float32 constants of the push, formed once on the host.
@@ -163,6 +164,10 @@ cudaError_t launch_load(const LoadArgs &a, int sms, cudaStream_t s);
 int make_load_args(const pic_loading *ld, long long n, double length, float *x, float *v,
                    LoadArgs *out);
 
+// Internal kernel choice of the fused push for the nearest-grid-point shape
+// (not a public deposit variant: PIC_SHAPE_NGP selects it).
+constexpr int kDepositNgp = 6;
+
 // Phase-space histogram (phase.cu).
 constexpr int kPhaseMaxBins = 16384;
 template <typename T>
@@ -176,6 +181,12 @@ struct PhaseArgs {
 };
 template <typename T>
 cudaError_t launch_phase(const PhaseArgs<T> &a, int sms, cudaStream_t s);
+
+// Range check of uploaded positions: sets kErrInput unless every x is in
+// [0, L) (phase.cu).
+template <typename T>
+cudaError_t launch_check_positions(const T *x, long long n, T length, unsigned *err, int sms,
+                                   cudaStream_t s);
 
 // Parameter checks shared by the single-run and the pool entry points.
 int validate_params(const pic_params *p);

@@ -23,6 +23,8 @@
 //   MATCH_PACKED  the two combined: one atomic per warp group;
 //   QUAD          runs of equal left node among a thread's 4 particles are
 //                 summed in registers, then two atomics per run.
+// The nearest-grid-point shape (PIC_SHAPE_NGP) uses the same loop with the
+// NGP gather and a QUAD-style deposit of whole particles to the cell's node.
 // The packed forms flush the tile to global memory before any node can hold
 // 2^16 particles, so the 40-bit weight field never carries into the count.
 // The unpacked tiles hold exact 64-bit sums in two 32-bit words (below).
@@ -136,10 +138,17 @@ __global__ void __launch_bounds__(512) pic_push_fixed_kernel(PushArgs a) {
             const bool valid = q < n4;
             float4 xx = cx[u], vv = cv[u];
             if (PUSH && valid) {
-                push_particle(xx.x, vv.x, sE, c, ke, mom);
-                push_particle(xx.y, vv.y, sE, c, ke, mom);
-                push_particle(xx.z, vv.z, sE, c, ke, mom);
-                push_particle(xx.w, vv.w, sE, c, ke, mom);
+                if (VARIANT == kDepositNgp) {
+                    push_particle_ngp(xx.x, vv.x, sE, c, ke, mom);
+                    push_particle_ngp(xx.y, vv.y, sE, c, ke, mom);
+                    push_particle_ngp(xx.z, vv.z, sE, c, ke, mom);
+                    push_particle_ngp(xx.w, vv.w, sE, c, ke, mom);
+                } else {
+                    push_particle(xx.x, vv.x, sE, c, ke, mom);
+                    push_particle(xx.y, vv.y, sE, c, ke, mom);
+                    push_particle(xx.z, vv.z, sE, c, ke, mom);
+                    push_particle(xx.w, vv.w, sE, c, ke, mom);
+                }
             }
             deposit4<VARIANT>(tile, xx, valid, c, a.err, lane);
             if (PUSH && valid) {
@@ -159,7 +168,10 @@ __global__ void __launch_bounds__(512) pic_push_fixed_kernel(PushArgs a) {
         const long long i = n4 * 4 + lane;
         const bool valid = i < a.n;
         float xs = valid ? a.x[i] : 0.0f, vs = valid && PUSH ? a.v[i] : 0.0f;
-        if (PUSH && valid) push_particle(xs, vs, sE, c, ke, mom);
+        if (PUSH && valid) {
+            if (VARIANT == kDepositNgp) push_particle_ngp(xs, vs, sE, c, ke, mom);
+            else push_particle(xs, vs, sE, c, ke, mom);
+        }
         deposit_one<VARIANT>(tile, xs, valid, c, a.err, lane);
         if (PUSH && valid) { a.x[i] = xs; a.v[i] = vs; }
     }
@@ -306,6 +318,7 @@ FixedKernel pick_fixed(int variant, bool push, int unroll) {
         case PIC_DEPOSIT_PACKED: return pick_unroll<PIC_DEPOSIT_PACKED>(push, unroll);
         case kMatchPacked: return pick_unroll<kMatchPacked>(push, unroll);
         case PIC_DEPOSIT_QUAD: return pick_unroll<PIC_DEPOSIT_QUAD>(push, unroll);
+        case kDepositNgp: return pick_unroll<kDepositNgp>(push, unroll);
         default: return nullptr;
     }
 }
@@ -324,7 +337,7 @@ cudaError_t push_prepare_attributes(int mode, int ng) {
     cudaError_t e = cudaSuccess;
     if (mode == PIC_FP32_FIXED) {
         const int unrolls[3] = {1, 2, 4};
-        for (int v = PIC_DEPOSIT_ATOMIC; v <= PIC_DEPOSIT_QUAD; v++)
+        for (int v = PIC_DEPOSIT_ATOMIC; v <= kDepositNgp; v++)
             for (int p = 0; p < 2; p++)
                 for (int u : unrolls) {
                     e = cudaFuncSetAttribute(pick_fixed(v, p != 0, u),

@@ -190,6 +190,9 @@ def test_bad_input_and_call_order():
     with pytest.raises(pic.PicError) as e:
         run.init(bad, np.zeros(n, np.float32))
     assert e.value.code == pic.PIC_EINVAL
+    with pytest.raises(pic.PicError) as e:       # a rejected upload leaves no state
+        run.push()
+    assert e.value.code == pic.PIC_ESTATE
     bad[7] = np.nan
     with pytest.raises(pic.PicError):
         run.init(bad, np.zeros(n, np.float32))
@@ -235,7 +238,7 @@ def test_autotune_leaves_state_and_results_unchanged():
     b.step_n(7)
     table = a.autotune(reps=2)
     assert len(table) >= 20 and (table["ms"] > 0).all()
-    g, blk, var = a.launch_shape()
+    g, blk, var, _ = a.launch_shape()
     best = table[np.argmin(table["ms"])]
     assert (var, blk) == (int(best["variant"]), int(best["block"]))
     xa, va = a.get_state()
