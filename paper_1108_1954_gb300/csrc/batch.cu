@@ -135,7 +135,7 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
         }
         {
             double kv[2] = {(double)ke, (double)mom};
-            block_sum_t<2, double>(kv, shd);
+            block_sum_f64k<2>(kv, shd);
             if (tid == 0) { ex.kv[0] = kv[0]; ex.kv[1] = kv[1]; }
         }
         cl.sync();                                                    // #1
@@ -226,7 +226,7 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
         const unsigned long long cq = rq;
         {
             double dv[1] = {d.fe};
-            block_sum_t<1, double>(dv, shd);
+            block_sum_f64k<1>(dv, shd);
             float md[2 * PIC_NMODES];
 #pragma unroll
             for (int m = 0; m < PIC_NMODES; m++) { md[2 * m] = d.re[m]; md[2 * m + 1] = d.im[m]; }
@@ -236,15 +236,21 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
             __shared__ unsigned long long cqw[32];
             if (lane == 0) cqw[tid >> 5] = cqb;
             __syncthreads();
-            if (tid == 0) {
-                unsigned long long t = 0;
-                for (int w = 0; w < (bs >> 5); w++) t += cqw[w];
-                ex.cq = t;
-                ex.diag[kDiagFE] = dv[0];
-                ex.diag[kDiagKE] = 0.0;
-                ex.diag[kDiagMom] = 0.0;
-                ex.diag[kDiagCharge] = r == 0 ? R.dx * R.k_rho * i128_to_f64(SR) : 0.0;
-                for (int m = 0; m < 2 * PIC_NMODES; m++) ex.diag[kDiagModes + m] = (double)md[m];
+            if (tid < 32) {
+                // lane m of warp 0 stores value m (md is complete in warp 0)
+                float mine = 0.0f;
+#pragma unroll
+                for (int m = 0; m < 2 * PIC_NMODES; m++) mine = (m == tid) ? md[m] : mine;
+                if (tid < 2 * PIC_NMODES) ex.diag[kDiagModes + tid] = (double)mine;
+                if (tid == 0) {
+                    unsigned long long t = 0;
+                    for (int w = 0; w < (bs >> 5); w++) t += cqw[w];
+                    ex.cq = t;
+                    ex.diag[kDiagFE] = dv[0];
+                    ex.diag[kDiagKE] = 0.0;
+                    ex.diag[kDiagMom] = 0.0;
+                    ex.diag[kDiagCharge] = r == 0 ? R.dx * R.k_rho * i128_to_f64(SR) : 0.0;
+                }
             }
         }
         cl.sync();                                                    // #3
@@ -283,25 +289,27 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
             }
         }
         __syncthreads();
-        if (r == 0 && tid == 0) {
-            long long n = step0 + s;
-            if (push) {
-                pic_diag_row *row = &R.hist[n % R.hist_len];
-                row->kinetic = 0.5 * R.mass * kvtot[0];
-                row->momentum = R.mass * kvtot[1];
-                n += 1;
-            }
+        if (r == 0 && tid < 32) {
+            // scalars by thread 0, mode m by thread m
+            const long long n = push ? step0 + s + 1 : step0 + s;
             pic_diag_row *row = &R.hist[n % R.hist_len];
-            const double qnan = __longlong_as_double(0x7ff8000000000000ll);
-            row->step = n;
-            row->kinetic = qnan;
-            row->momentum = qnan;
-            row->field = 0.5 * R.dx * tot[kDiagFE];
-            row->charge = tot[kDiagCharge];
-            row->charge_q = (long long)cqt;
-            for (int m = 0; m < PIC_NMODES; m++) {
-                const double re = tot[kDiagModes + 2 * m], im = tot[kDiagModes + 2 * m + 1];
-                row->mode[m] = 2.0 * sqrt(re * re + im * im) / (double)ng;
+            if (tid == 0) {
+                if (push) {
+                    pic_diag_row *prev = &R.hist[(step0 + s) % R.hist_len];
+                    prev->kinetic = 0.5 * R.mass * kvtot[0];
+                    prev->momentum = R.mass * kvtot[1];
+                }
+                const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+                row->step = n;
+                row->kinetic = qnan;
+                row->momentum = qnan;
+                row->field = 0.5 * R.dx * tot[kDiagFE];
+                row->charge = tot[kDiagCharge];
+                row->charge_q = (long long)cqt;
+            }
+            if (tid < PIC_NMODES) {
+                const double re = tot[kDiagModes + 2 * tid], im = tot[kDiagModes + 2 * tid + 1];
+                row->mode[tid] = 2.0 * sqrt(re * re + im * im) / (double)ng;
             }
         }
         __syncthreads();

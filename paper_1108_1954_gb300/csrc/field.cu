@@ -148,31 +148,6 @@ __device__ void finalize(const SolveArgs &a, long long step) {
 
 // ---- the cluster solves' common parts -------------------------------------
 
-// Sum of one float64 per thread over a block (warp trees, then warp 0 over
-// the warp sums); valid in lane 0 of warp 0.  Adds in predicated lanes only,
-// since float64 issue is scarce on GB300.
-__device__ __forceinline__ double block_sum_f64(double v, double *slot /*[32]*/) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const double u = __shfl_down_sync(kFull, v, o);
-        if (lane < o) v += u;
-    }
-    if (lane == 0) slot[w] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (w == 0) {
-        s = lane < nw ? slot[lane] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            if (o >= nw) continue;            // warp-uniform: only the levels nw needs
-            const double u = __shfl_down_sync(kFull, s, o);
-            if (lane < o) s += u;
-        }
-    }
-    return s;
-}
-
 // Sum over the cluster of the blocks' values *pub (each published by its
 // block before the caller's cluster barrier), the same fixed tree over the
 // ranks in every warp of every block: every thread gets the same total.

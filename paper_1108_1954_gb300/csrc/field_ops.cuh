@@ -105,6 +105,47 @@ static __device__ void block_sum_t(T (&v)[K], T *sh /*[32*K]*/) {
     __syncthreads();
 }
 
+// Sums of K float64 values per thread over a block (warp trees, then warp 0
+// over the warp sums), valid in lane 0 of warp 0.  The adds run in the
+// predicated lanes only (31 lane-adds per warp and value instead of 160):
+// GB300 issues float64 at 2 lanes per clock per SM, so the full butterfly
+// of block_sum_t costs more than the rest of a small solve.
+template <int K>
+__device__ __forceinline__ void block_sum_f64k(double (&v)[K], double *slot /*[32*K]*/) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int i = 0; i < K; i++) {
+            const double u = __shfl_down_sync(kFull, v[i], o);
+            if (lane < o) v[i] += u;
+        }
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < K; i++) slot[w * K + i] = v[i];
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int i = 0; i < K; i++) v[i] = lane < nw ? slot[lane * K + i] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            if (o >= nw) continue;            // warp-uniform: only the levels nw needs
+#pragma unroll
+            for (int i = 0; i < K; i++) {
+                const double u = __shfl_down_sync(kFull, v[i], o);
+                if (lane < o) v[i] += u;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ double block_sum_f64(double v, double *slot /*[32]*/) {
+    double a[1] = {v};
+    block_sum_f64k<1>(a, slot);
+    return a[0];
+}
+
 // Per-node diagnostics contribution of node g with field E (float64) and its
 // float32 copy: field energy sum and the mode sums (float32 twiddles).
 struct NodeDiag {
