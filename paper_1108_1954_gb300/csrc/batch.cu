@@ -57,6 +57,8 @@ template <int VARIANT>
 __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_group &cl,
                           Exchange &ex, Tile &tile, float *sE, i128 *sh128, double *shd,
                           float *shf, double *kvtot) {
+    __shared__ i128 wlast[32];
+    __shared__ i128 pre[4];
     const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
     const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31;
     const PushConsts c = R.pc;
@@ -154,15 +156,28 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
         // one node per thread: g = b0 + tid (the pool keeps ceil(NG/C) <= block)
         const int g = b0 + tid;
         const bool mine = g < b1;
+        // the C blocks' words for this node, all remote loads issued together
         unsigned long long rq = 0;
         if (mine) {
-            for (int b = 0; b < C; b++) {
-                const unsigned *plo = cl.map_shared_rank(tile.lo, b);
-                const unsigned *phi = cl.map_shared_rank(tile.hi, b);
-                rq += ((unsigned long long)phi[g + 1] << 32) | plo[g + 1];
-                if (g == ng - 1) rq += ((unsigned long long)phi[0] << 32) | plo[0];
-                if (g == 0) rq += ((unsigned long long)phi[ng + 1] << 32) | plo[ng + 1];
+            unsigned lo[kMaxCluster], hi[kMaxCluster];
+#pragma unroll
+            for (int b = 0; b < kMaxCluster; b++) {
+                lo[b] = b < C ? cl.map_shared_rank(tile.lo, b)[g + 1] : 0u;
+                hi[b] = b < C ? cl.map_shared_rank(tile.hi, b)[g + 1] : 0u;
             }
+#pragma unroll
+            for (int b = 0; b < kMaxCluster; b++)
+                rq += ((unsigned long long)hi[b] << 32) | lo[b];
+            // the ghost words: index 0 (node -1) folds onto node NG-1, index
+            // NG+1 (node NG) onto node 0
+            if (g == ng - 1)
+                for (int b = 0; b < C; b++)
+                    rq += ((unsigned long long)cl.map_shared_rank(tile.hi, b)[0] << 32) |
+                          cl.map_shared_rank(tile.lo, b)[0];
+            if (g == 0)
+                for (int b = 0; b < C; b++)
+                    rq += ((unsigned long long)cl.map_shared_rank(tile.hi, b)[ng + 1] << 32) |
+                          cl.map_shared_rank(tile.lo, b)[ng + 1];
         }
         const i128 Rg = mine ? (i128)ntot - (i128)ng * (i128)rq : (i128)0;
         {
@@ -172,24 +187,26 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
         }
         cl.sync();                                                    // #2
 
-        // prefixes from the slice sums of all blocks, in rank order (the
-        // C remote reads issued together)
-        i128 A0 = 0, B = 0, SR = 0, SS1 = 0;
-        {
-            i128 t0[kMaxCluster], t1[kMaxCluster];
-#pragma unroll
-            for (int b = 0; b < kMaxCluster; b++) {
-                const Exchange *pe = cl.map_shared_rank(&ex, b < C ? b : 0);
-                t0[b] = b < C ? pe->s0 : (i128)0;
-                t1[b] = b < C ? pe->s1 : (i128)0;
+        // prefixes from the slice sums of all blocks: one remote read per
+        // lane of warp 0 (integer sums, so the order does not matter)
+        if (tid < 32) {
+            i128 v0 = 0, v1 = 0;
+            if (tid < C) {
+                const Exchange *pe = cl.map_shared_rank(&ex, tid);
+                v0 = pe->s0;
+                v1 = pe->s1;
             }
-#pragma unroll
-            for (int b = 0; b < kMaxCluster; b++) {
-                if (b < r) { A0 += t0[b]; B += t1[b]; }
-                SR += t0[b];
-                SS1 += t1[b];
+            i128 a0 = tid < r ? v0 : (i128)0, bb = tid < r ? v1 : (i128)0;
+            for (int o = 16; o > 0; o >>= 1) {
+                a0 += shfl_down_i128(a0, o);
+                bb += shfl_down_i128(bb, o);
+                v0 += shfl_down_i128(v0, o);
+                v1 += shfl_down_i128(v1, o);
             }
+            if (tid == 0) { pre[0] = a0; pre[1] = bb; pre[2] = v0; pre[3] = v1; }
         }
+        __syncthreads();
+        const i128 A0 = pre[0], B = pre[1], SR = pre[2], SS1 = pre[3];
         const i128 SP = (i128)ng * SR - SS1;          // sum_k (NG-k) R_k
         const i128 A1 = (i128)b0 * A0 - B;             // sum_{k<b0} (b0-k) R_k
         i128 tot_;
@@ -199,7 +216,6 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
         const i128 M = (i128)ng * Pg - SP;                                  // M_g
         // M_{g-1}: previous thread, or the slice's left neighbour for tid 0
         i128 Mprev = shfl_up_i128(M, 1);
-        __shared__ i128 wlast[32];
         if (lane == 31) wlast[tid >> 5] = M;
         __syncthreads();
         if (lane == 0)
@@ -255,13 +271,27 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
         }
         cl.sync();                                                    // #3
 
-        // ---- C: the other slices of E into the own copy; history rows
-        for (int j = tid; j < ng + 2; j += bs) {
-            const int g = j == 0 ? ng - 1 : (j == ng + 1 ? 0 : j - 1);
-            const int owner = g / P;
-            if (owner != r) sE[j] = cl.map_shared_rank(sE, owner)[j];
-            tile.lo[j] = 0u;
-            tile.hi[j] = 0u;
+        // ---- C: the other slices of E into the own copy (kCopy remote
+        // loads in flight per thread); history rows
+        constexpr int kCopy = 8;
+        for (int j0 = tid; j0 < ng + 2; j0 += kCopy * bs) {
+            float e[kCopy];
+#pragma unroll
+            for (int k = 0; k < kCopy; k++) {
+                const int j = j0 + k * bs;
+                const int g = j == 0 ? ng - 1 : (j == ng + 1 ? 0 : j - 1);
+                const int owner = g / P;
+                e[k] = (j < ng + 2 && owner != r) ? cl.map_shared_rank(sE, owner)[j] : 0.0f;
+            }
+#pragma unroll
+            for (int k = 0; k < kCopy; k++) {
+                const int j = j0 + k * bs;
+                if (j >= ng + 2) break;
+                const int g = j == 0 ? ng - 1 : (j == ng + 1 ? 0 : j - 1);
+                if (g / P != r) sE[j] = e[k];
+                tile.lo[j] = 0u;
+                tile.hi[j] = 0u;
+            }
         }
         // block 0: field f of the diagnostics summed over the blocks by
         // thread f (rank order), then one thread writes the history rows
