@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--weak-steps", type=int, default=1000)
     ap.add_argument("--only-weak", action="store_true",
                     help="run only the paper's weak-scaling workload")
+    ap.add_argument("--only-c1", action="store_true",
+                    help="run only the config-1 latency section")
     ap.add_argument("--only-batched", action="store_true",
                     help="run only the batched-ensemble section (profiling)")
     ap.add_argument("--no-tune-batched", action="store_true")
@@ -339,7 +341,7 @@ def tune_pool(states, steps, history):
     pool.sync()
     table = []
     e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
-    for variant in (1, 2, 5, 1 + 16, 2 + 16, 5 + 16):
+    for variant in (1, 2, 5, 6, 1 + 16, 2 + 16, 5 + 16, 6 + 16):
         for cluster in (4, 8):
             for block in (256, 512):
                 try:
@@ -366,7 +368,7 @@ def time_batched(args):
     states = ensemble_states(args.batched_runs, 3)
     total_particles = sum(p.npart for p, _, _ in states)
     if args.no_tune_batched:
-        best, table = (5 + 16, 8, 512), []
+        best, table = (1 + 16, 8, 256), []
     else:
         best, table = tune_pool(states, 10, H)
     nbytes = sum(pic.pool_run_bytes(p, H) for p, _, _ in states) + (64 << 20)
@@ -485,7 +487,7 @@ def variant_scan(args):
         xs, vs = run.get_state()
         st = run.step
         row = {"step": st}
-        for var in (1, 2, 5):
+        for var in (1, 2, 5, 6):
             for blk, un in ((512, 1), (512, 2), (256, 1)):
                 run.set_state(xs, vs, st)
                 run.set_launch(var, blk, un)
@@ -717,6 +719,9 @@ def main():
         return
     if args.only_weak:
         print(json.dumps({"weak": time_weak(args)}))
+        return
+    if args.only_c1:
+        print(json.dumps({"c1": time_c1(args)}))
         return
     x32, v32 = make_state(w)
     res = time_ours(args, w, x32, v32)

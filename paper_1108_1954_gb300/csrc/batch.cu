@@ -387,6 +387,7 @@ BatchKernel pick_batch_minb(int variant) {
         case PIC_DEPOSIT_ATOMIC: return &pic_batch_kernel<PIC_DEPOSIT_ATOMIC, MINB>;
         case PIC_DEPOSIT_MATCH: return &pic_batch_kernel<PIC_DEPOSIT_MATCH, MINB>;
         case PIC_DEPOSIT_QUAD: return &pic_batch_kernel<PIC_DEPOSIT_QUAD, MINB>;
+        case PIC_DEPOSIT_PAIR: return &pic_batch_kernel<PIC_DEPOSIT_PAIR, MINB>;
         default: return nullptr;
     }
 }
@@ -407,7 +408,7 @@ size_t batch_smem_bytes(int ng_max, int cluster, int block) {
 
 cudaError_t batch_prepare_attributes() {
     const int bytes = (int)batch_smem_bytes(PIC_NCELL_MAX, 8, 512);
-    const int vs[3] = {PIC_DEPOSIT_ATOMIC, PIC_DEPOSIT_MATCH, PIC_DEPOSIT_QUAD};
+    const int vs[4] = {PIC_DEPOSIT_ATOMIC, PIC_DEPOSIT_MATCH, PIC_DEPOSIT_QUAD, PIC_DEPOSIT_PAIR};
     for (int v : vs)
         for (int m = 0; m < 2; m++) {
             cudaError_t e = cudaFuncSetAttribute(pick_batch(v + 16 * m),

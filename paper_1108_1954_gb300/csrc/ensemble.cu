@@ -72,7 +72,8 @@ int check_cfg(const pic_pool_config *c) {
 int check_shape(int code, int cluster, int block, int ncell_max) {
     const int variant = code & 15;
     if (code >> 4 > 1) return PIC_EINVAL;
-    if (variant != PIC_DEPOSIT_ATOMIC && variant != PIC_DEPOSIT_MATCH && variant != PIC_DEPOSIT_QUAD)
+    if (variant != PIC_DEPOSIT_ATOMIC && variant != PIC_DEPOSIT_MATCH && variant != PIC_DEPOSIT_QUAD &&
+        variant != PIC_DEPOSIT_PAIR)
         return PIC_EINVAL;
     if (cluster != 1 && cluster != 2 && cluster != 4 && cluster != 8) return PIC_EINVAL;
     if (block < 128 || block > 512 || block % 32) return PIC_EINVAL;

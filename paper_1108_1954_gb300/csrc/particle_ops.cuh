@@ -134,7 +134,8 @@ __device__ __forceinline__ void deposit_one(const Tile &t, float x, bool valid,
     const bool ok = valid && l.j <= (unsigned)c.ng;
     if (valid && !ok) atomicOr(err, kErrPosition);
     const unsigned W = ok ? fixed_weight(l.f) : 0u;
-    if (VARIANT == PIC_DEPOSIT_ATOMIC || VARIANT == PIC_DEPOSIT_QUAD) {
+    if (VARIANT == PIC_DEPOSIT_ATOMIC || VARIANT == PIC_DEPOSIT_QUAD ||
+        VARIANT == PIC_DEPOSIT_PAIR) {
         if (ok) {
             tile_add(t, l.j, kFixOne - W);
             tile_add(t, l.j + 1, W);
@@ -181,6 +182,36 @@ __device__ __forceinline__ void deposit4(const Tile &t, const float4 &xx, bool v
             }
         }
         if (key != 0xffffffffu) tile_add(t, key, cnt);
+        if (bad) atomicOr(err, kErrPosition);
+    } else if (VARIANT == PIC_DEPOSIT_PAIR) {
+        // two open runs (key, left, right); a third key closes run a
+        unsigned ka = 0xffffffffu, la = 0, ra = 0, kb = 0xffffffffu, lb = 0, rb = 0;
+        bool bad = false;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const Loc l = locate(xs[k], c.inv_dx);
+            const bool ok = valid && l.j <= (unsigned)c.ng;
+            bad |= valid && !ok;
+            const unsigned W = fixed_weight(l.f);
+            if (!ok) continue;
+            if (l.j == ka) {
+                la += kFixOne - W;
+                ra += W;
+            } else if (l.j == kb) {
+                lb += kFixOne - W;
+                rb += W;
+            } else if (ka == 0xffffffffu) {
+                ka = l.j; la = kFixOne - W; ra = W;
+            } else if (kb == 0xffffffffu) {
+                kb = l.j; lb = kFixOne - W; rb = W;
+            } else {
+                tile_add(t, ka, la);
+                tile_add(t, ka + 1, ra);
+                ka = l.j; la = kFixOne - W; ra = W;
+            }
+        }
+        if (ka != 0xffffffffu) { tile_add(t, ka, la); tile_add(t, ka + 1, ra); }
+        if (kb != 0xffffffffu) { tile_add(t, kb, lb); tile_add(t, kb + 1, rb); }
         if (bad) atomicOr(err, kErrPosition);
     } else if (VARIANT == PIC_DEPOSIT_QUAD) {
         // consecutive particles of the group with equal left node are summed

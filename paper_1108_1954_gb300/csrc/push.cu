@@ -22,7 +22,10 @@
 //                 word per left node, unpacked when the tile is flushed;
 //   MATCH_PACKED  the two combined: one atomic per warp group;
 //   QUAD          runs of equal left node among a thread's 4 particles are
-//                 summed in registers, then two atomics per run.
+//                 summed in registers, then two atomics per run;
+//   PAIR          the same with two open runs, so that particles of two
+//                 interleaved cells (the two beams before the first sort)
+//                 still combine.
 // The nearest-grid-point shape (PIC_SHAPE_NGP) uses the same loop with the
 // NGP gather and a QUAD-style deposit of whole particles to the cell's node.
 // The packed forms flush the tile to global memory before any node can hold
@@ -318,6 +321,7 @@ FixedKernel pick_fixed(int variant, bool push, int unroll) {
         case PIC_DEPOSIT_PACKED: return pick_unroll<PIC_DEPOSIT_PACKED>(push, unroll);
         case kMatchPacked: return pick_unroll<kMatchPacked>(push, unroll);
         case PIC_DEPOSIT_QUAD: return pick_unroll<PIC_DEPOSIT_QUAD>(push, unroll);
+        case PIC_DEPOSIT_PAIR: return pick_unroll<PIC_DEPOSIT_PAIR>(push, unroll);
         case kDepositNgp: return pick_unroll<kDepositNgp>(push, unroll);
         default: return nullptr;
     }

@@ -99,7 +99,7 @@ def test_one_step_parity(n, ng):
     one_step_parity(n, ng, L4PI, seed=n + ng)
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("block", [64, 256, 512])
 @pytest.mark.parametrize("unroll", [1, 2, 4])
 def test_deposit_variants_and_shapes_identical(variant, block, unroll):
