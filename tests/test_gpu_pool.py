@@ -11,7 +11,6 @@ import math
 import numpy as np
 import pytest
 
-import oracle as O
 import paper_1108_1954_gb300 as pic  # noqa: E402
 import torch  # noqa: E402,F401
 import workloads as W
