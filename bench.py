@@ -265,10 +265,29 @@ def time_ours(args, w, x32, v32):
         one_step(evs[i])
     torch.cuda.synchronize()
     push_ms = [a.elapsed_time(b) for a, b in evs]
+    # the floor of the push's memory traffic: the same bytes (x and v of N
+    # particles, float32, read and written in place) streamed by torch's
+    # elementwise kernel
+    xa = torch.empty(n, dtype=torch.float32, device=run.device).uniform_()
+    va = torch.empty(n, dtype=torch.float32, device=run.device).uniform_()
+    fl = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(20)]
+    cs = torch.cuda.current_stream()
+    for i in range(23):
+        if i >= 3:
+            fl[i - 3][0].record(cs)
+        xa.mul_(1.0)
+        va.mul_(1.0)
+        if i >= 3:
+            fl[i - 3][1].record(cs)
+    torch.cuda.synchronize()
+    floor_ms = statistics.mean(a.elapsed_time(b) for a, b in fl)
+    del xa, va
     run.sync()
     grid, block, variant, unroll = run.launch_shape()
     diag = run.diagnostics(run.step - 1, 1)[0]
-    res = dict(total_ms=total_ms, push_ms=push_ms, clocks=ck, launches=timed_launches,
+    res = dict(total_ms=total_ms, push_ms=push_ms, floor_ms=floor_ms, clocks=ck,
+               launches=timed_launches,
                grid=grid, block=block, variant=variant, unroll=unroll,
                blocks_per_sm=grid // max(1, torch.cuda.get_device_properties(0).multi_processor_count),
                steps=K,
@@ -487,8 +506,10 @@ def variant_scan(args):
         xs, vs = run.get_state()
         st = run.step
         row = {"step": st}
-        for var in (1, 2, 5, 6):
+        for var in (1, 2, 5, 6, 7):
             for blk, un in ((512, 1), (512, 2), (256, 1)):
+                if var == 7 and (blk, un) != (512, 1):
+                    continue          # the bulk-copy kernel has one shape
                 run.set_state(xs, vs, st)
                 run.set_launch(var, blk, un)
                 ev = [(torch.cuda.Event(True), torch.cuda.Event(True)) for _ in range(2 * S)]
@@ -769,7 +790,11 @@ def main():
                                            for i in range(0, len(res["push_ms"]), 100)],
                      "push_timing": "CUDA events around each push on the run's stream, over "
                                     "the K steps that follow the timed region, one call per "
-                                    "kernel"},
+                                    "kernel",
+                     "copy_floor_ms": res["floor_ms"],
+                     "copy_floor": "the same 16 B per particle (x, v float32 read and written "
+                                   "in place) streamed by torch's elementwise kernel "
+                                   "(x.mul_(1); v.mul_(1))"},
         "timing": "value: CUDA events around pic_step_n(K) (CUDA graphs of whole sort "
                   "periods) on the run's stream, after warm-up and graph capture",
         "gpu_launches": res["launches"],

@@ -76,6 +76,10 @@ extern "C" {
 #define PIC_DEPOSIT_PAIR 6         /* QUAD with two open runs per thread, so
                                       particles of two interleaved cells (two
                                       beams before a sort) still combine    */
+#define PIC_DEPOSIT_QUAD_BULK 7    /* QUAD, with the particle tiles moved
+                                      between HBM and shared memory by bulk
+                                      copies (cp.async.bulk, mbarrier); 512
+                                      threads, unroll 1                     */
 
 /* Field solvers (pic_params.field_solver).  Both solve the Eq. 6 system with
  * Phi_0 = 0 (the gauge the paper pins).
@@ -260,7 +264,7 @@ int pic_phase_space(pic_run *run, int32_t nx, int32_t nv, double vmin, double vm
 int pic_device_arrays(pic_run *run, void **x, void **v, void **E32);
 
 /* The launch shape the run uses for its fused push (any pointer may be
- * NULL): grid, threads per block, deposit variant (7: the NGP shape's
+ * NULL): grid, threads per block, deposit variant (15: the NGP shape's
  * kernel), float4 groups per thread per iteration. */
 int pic_launch_shape(const pic_run *run, int32_t *grid, int32_t *block,
                      int32_t *variant, int32_t *unroll);

@@ -31,7 +31,7 @@ PIC_ETIMEOUT, PIC_EDEVICE, PIC_ESTATE = -4, -5, -6
 PIC_FP32_FIXED, PIC_FP32_ATOMIC, PIC_FP64 = 0, 1, 2
 PIC_DEPOSIT_AUTO, PIC_DEPOSIT_ATOMIC, PIC_DEPOSIT_MATCH = 0, 1, 2
 PIC_DEPOSIT_PACKED, PIC_DEPOSIT_MATCH_PACKED, PIC_DEPOSIT_QUAD = 3, 4, 5
-PIC_DEPOSIT_PAIR = 6
+PIC_DEPOSIT_PAIR, PIC_DEPOSIT_QUAD_BULK = 6, 7
 PIC_SOLVER_EXACT, PIC_SOLVER_CG = 0, 1
 PIC_SHAPE_CIC, PIC_SHAPE_NGP = 0, 1
 PIC_CG_DEFAULT_ITERATIONS = 150
@@ -42,7 +42,8 @@ FIX_BITS = 24
 VARIANT_NAMES = {PIC_DEPOSIT_ATOMIC: "atomic", PIC_DEPOSIT_MATCH: "match",
                  PIC_DEPOSIT_PACKED: "packed",
                  PIC_DEPOSIT_MATCH_PACKED: "match_packed",
-                 PIC_DEPOSIT_QUAD: "quad", PIC_DEPOSIT_PAIR: "pair"}
+                 PIC_DEPOSIT_QUAD: "quad", PIC_DEPOSIT_PAIR: "pair",
+                 PIC_DEPOSIT_QUAD_BULK: "quad_bulk"}
 
 
 class CParams(C.Structure):

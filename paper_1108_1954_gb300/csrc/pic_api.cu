@@ -38,7 +38,7 @@ int pic::validate_params(const pic_params *p) {
     if (!finite_pos(p->length) || !finite_pos(p->dt) || !finite_pos(p->rho_ion)) return PIC_EINVAL;
     if (!std::isfinite(p->qm) || !(p->qm < 0.0)) return PIC_EINVAL;
     if (p->sort_interval < 0 || p->history < 0) return PIC_EINVAL;
-    if (p->deposit_variant < PIC_DEPOSIT_AUTO || p->deposit_variant > PIC_DEPOSIT_PAIR) return PIC_EINVAL;
+    if (p->deposit_variant < PIC_DEPOSIT_AUTO || p->deposit_variant > PIC_DEPOSIT_QUAD_BULK) return PIC_EINVAL;
     if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 1024 || p->block_size % 32)) return PIC_EINVAL;
     if (p->precision == PIC_FP32_FIXED && p->block_size > 512) return PIC_EINVAL;
     if (p->blocks_per_sm < 0 || p->blocks_per_sm > 32) return PIC_EINVAL;
@@ -662,7 +662,7 @@ int pic_set_launch(pic_run *run, int32_t variant, int32_t block, int32_t unroll,
     const int v = variant ? variant : run->variant;
     const int b = block ? block : run->block;
     const int u = unroll ? unroll : run->unroll;
-    if (!ngp && (v < PIC_DEPOSIT_ATOMIC || v > PIC_DEPOSIT_PAIR || (!fixed && v != PIC_DEPOSIT_ATOMIC)))
+    if (!ngp && (v < PIC_DEPOSIT_ATOMIC || v > PIC_DEPOSIT_QUAD_BULK || (!fixed && v != PIC_DEPOSIT_ATOMIC)))
         return PIC_EINVAL;
     if (b < 32 || b % 32 || b > (fixed ? 512 : 1024)) return PIC_EINVAL;
     if ((u != 1 && u != 2 && u != 4) || (!fixed && u != 1)) return PIC_EINVAL;
@@ -684,7 +684,8 @@ int pic_autotune(pic_run *run, int32_t reps, pic_tune_entry *results,
     if (nresults) *nresults = 0;
     if (run->p.precision != PIC_FP32_FIXED) return PIC_OK;
     static const int variants[] = {PIC_DEPOSIT_ATOMIC, PIC_DEPOSIT_MATCH, PIC_DEPOSIT_PACKED,
-                                   PIC_DEPOSIT_MATCH_PACKED, PIC_DEPOSIT_QUAD, PIC_DEPOSIT_PAIR};
+                                   PIC_DEPOSIT_MATCH_PACKED, PIC_DEPOSIT_QUAD, PIC_DEPOSIT_PAIR,
+                                   PIC_DEPOSIT_QUAD_BULK};
     static const int ngp_only[] = {kDepositNgp};
     static const int blocks[] = {128, 256, 512};
     static const int unrolls[] = {1, 2};

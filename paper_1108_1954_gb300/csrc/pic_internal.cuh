@@ -166,7 +166,7 @@ int make_load_args(const pic_loading *ld, long long n, double length, float *x, 
 
 // Internal kernel choice of the fused push for the nearest-grid-point shape
 // (not a public deposit variant: PIC_SHAPE_NGP selects it).
-constexpr int kDepositNgp = 7;
+constexpr int kDepositNgp = 15;
 
 // Phase-space histogram (phase.cu).
 constexpr int kPhaseMaxBins = 16384;

@@ -96,7 +96,7 @@ def test_ngp_guards():
         run.set_launch(variant=pic.PIC_DEPOSIT_ATOMIC)
     run.set_launch(block=256)
     tune = run.autotune(reps=2)
-    assert len(tune) > 0 and (tune["variant"] == 7).all()      # the NGP kernel
+    assert len(tune) > 0 and (tune["variant"] == 15).all()     # the NGP kernel
     pool = pic.Pool(max_slots=2, ncell_max=64, arena_bytes=1 << 24, history=4)
     with pytest.raises(pic.PicError):
         pool.admit(pic.Params(npart=n, ncell=ng, length=L4PI, shape=pic.PIC_SHAPE_NGP),

@@ -250,3 +250,27 @@ def test_autotune_leaves_state_and_results_unchanged():
     xb, vb = b.get_state()
     assert np.array_equal(xa, xb) and np.array_equal(va, vb)
     assert np.array_equal(a.get_field()["rho_q"], b.get_field()["rho_q"])
+
+
+@pytest.mark.parametrize("n,ng", [(1, 16), (2047, 64), (2048, 64), (2049, 64),
+                                  (70001, 512), (300000, 4096), (100003, 8192)])
+def test_bulk_copy_push_identical(n, ng):
+    # the bulk-copy push (tiles of 2048 particles through shared memory, the
+    # tail through the per-thread path) gives the particles and the integer
+    # density of the per-thread kernels bit for bit
+    x, v = W.two_stream(n, L4PI, 0.2, 0.01, 5 + n)
+    x32, v32 = W.to_f32_state(x, v, L4PI)
+    ref = make_run(n, ng, L4PI, deposit_variant=1, block_size=256, sort_interval=4)
+    ref.init(x32, v32)
+    ref.step_n(9)
+    run = make_run(n, ng, L4PI, deposit_variant=pic.PIC_DEPOSIT_QUAD_BULK, block_size=512,
+                   unroll=1, sort_interval=4)
+    run.init(x32, v32)
+    run.step_n(9)
+    assert np.array_equal(run.get_field()["rho_q"], ref.get_field()["rho_q"])
+    xa, va = run.get_state()
+    xb, vb = ref.get_state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    assert run.launch_shape()[2] == pic.PIC_DEPOSIT_QUAD_BULK
+    da, db = run.diagnostics(0, 9), ref.diagnostics(0, 9)
+    assert np.allclose(da["kinetic"], db["kinetic"], rtol=1e-5)
