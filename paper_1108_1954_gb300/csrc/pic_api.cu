@@ -82,6 +82,7 @@ void sort_geometry(int64_t n, int ng, int *nchunk, long long *chunk, int *nseg, 
     if (nc > cap_tab) nc = cap_tab;
     if (nc < 1) nc = 1;
     long long ch = (n + nc - 1) / nc;
+    ch = (ch + 3) & ~3ll;                   // chunks start on float4 groups
     nc = (n + ch - 1) / ch;
     int ns = 1;
     while ((long long)ns * ns < nc) ns++;   // nseg, seg_len <= 32 (nchunk <= 1024)

@@ -42,18 +42,56 @@ __global__ void __launch_bounds__(kSortThreads) sort_count_kernel(SortArgs<T> a)
     __syncthreads();
     const long long start = (long long)blockIdx.x * a.chunk;
     const long long end = min(a.n, start + a.chunk);
-    constexpr int K = 8;   // loads in flight per thread
-    for (long long i0 = start; i0 < end; i0 += K * blockDim.x) {
-        T xv[K];
+    if (sizeof(T) == 4 && (a.chunk & 3) == 0) {
+        // float4 groups (the chunk starts on a group): equal cells among a
+        // group's 4 particles are counted with one atomic, K groups in flight
+        constexpr int K = 4;
+        const float4 *x4 = reinterpret_cast<const float4 *>(a.x);
+        const long long q0 = start >> 2, q1 = end >> 2;
+        for (long long qb = q0; qb < q1; qb += K * blockDim.x) {
+            float4 xv[K];
 #pragma unroll
-        for (int k = 0; k < K; k++) {
-            const long long i = i0 + k * blockDim.x + threadIdx.x;
-            xv[k] = i < end ? __ldcs(a.x + i) : (T)0;
+            for (int k = 0; k < K; k++) {
+                const long long q = qb + k * blockDim.x + threadIdx.x;
+                xv[k] = q < q1 ? __ldcs(x4 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                const long long q = qb + k * blockDim.x + threadIdx.x;
+                if (q >= q1) continue;
+                const float xs[4] = {xv[k].x, xv[k].y, xv[k].z, xv[k].w};
+                unsigned key = cell_key((T)xs[0], a.inv_dx, ng), run = 1u;
+#pragma unroll
+                for (int j = 1; j < 4; j++) {
+                    const unsigned kj = cell_key((T)xs[j], a.inv_dx, ng);
+                    if (kj == key) {
+                        run++;
+                    } else {
+                        atomicAdd(&sh_count[key], run);
+                        key = kj;
+                        run = 1u;
+                    }
+                }
+                atomicAdd(&sh_count[key], run);
+            }
         }
+        // the chunk's last n mod 4 particles
+        const long long i = (q1 << 2) + threadIdx.x;
+        if (i < end) atomicAdd(&sh_count[cell_key(a.x[i], a.inv_dx, ng)], 1u);
+    } else {
+        constexpr int K = 8;   // loads in flight per thread
+        for (long long i0 = start; i0 < end; i0 += K * blockDim.x) {
+            T xv[K];
 #pragma unroll
-        for (int k = 0; k < K; k++) {
-            const long long i = i0 + k * blockDim.x + threadIdx.x;
-            if (i < end) atomicAdd(&sh_count[cell_key(xv[k], a.inv_dx, ng)], 1u);
+            for (int k = 0; k < K; k++) {
+                const long long i = i0 + k * blockDim.x + threadIdx.x;
+                xv[k] = i < end ? __ldcs(a.x + i) : (T)0;
+            }
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                const long long i = i0 + k * blockDim.x + threadIdx.x;
+                if (i < end) atomicAdd(&sh_count[cell_key(xv[k], a.inv_dx, ng)], 1u);
+            }
         }
     }
     __syncthreads();

@@ -64,6 +64,7 @@ void geometry(long long n, int nchunk_max, int *nchunk, long long *chunk, int *n
     if (nc < 1) nc = 1;
     if (nc > nchunk_max) nc = nchunk_max;
     long long ch = (n + nc - 1) / nc;
+    ch = (ch + 3) & ~3ll;                   // chunks start on float4 groups
     nc = (n + ch - 1) / ch;
     int ns = 1;
     while ((long long)ns * ns < nc) ns++;
