@@ -198,33 +198,57 @@ __device__ __forceinline__ void push_sums_share(const SolveArgs &a, int C, int r
 __device__ void cluster_finish(const SolveArgs &a, cg::cluster_group &cl, ClusterDiag &cd,
                                const double (&kv)[2], const NodeDiag &d, double charge,
                                unsigned long long q, long long step) {
-    __shared__ double shd[32];
-    __shared__ float shf[32 * 2 * PIC_NMODES];
-    __shared__ unsigned long long cqw[32];
+    __shared__ __align__(16) double shd[32];
+    __shared__ __align__(16) float shf[2 * PIC_NMODES][32];       // [value][warp]
+    __shared__ __align__(16) unsigned long long cqw[32];
     const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
-    const int T = blockDim.x, t = threadIdx.x, lane = t & 31;
-    const double fe = block_sum_f64(d.fe, shd);
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = blockDim.x >> 5;
+    // The block's sums of the field energy (float64), the mode sums (float32)
+    // and the integer charge with one barrier: warp sums by shuffles, then
+    // warp 0 across the warps -- the field energy by the predicated float64
+    // tree, each mode sum by one lane in warp order.
+    double fe = d.fe;
+    unsigned long long cqb = q;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double u = __shfl_down_sync(kFull, fe, o);
+        if (lane < o) fe += u;
+        cqb += __shfl_down_sync(kFull, cqb, o);
+    }
     float md[2 * PIC_NMODES];
 #pragma unroll
     for (int m = 0; m < PIC_NMODES; m++) { md[2 * m] = d.re[m]; md[2 * m + 1] = d.im[m]; }
-    block_sum_t<2 * PIC_NMODES, float>(md, shf);
-    unsigned long long cqb = q;
-    for (int o = 16; o > 0; o >>= 1) cqb += __shfl_down_sync(kFull, cqb, o);
-    if (lane == 0) cqw[t >> 5] = cqb;
-    __syncthreads();
-    if (t < 32) {
-        // lane m of warp 0 stores value m (md is complete in warp 0)
-        float mine = 0.0f;
 #pragma unroll
-        for (int m = 0; m < 2 * PIC_NMODES; m++) mine = (m == t) ? md[m] : mine;
-        if (t < 2 * PIC_NMODES) cd.diag[kDiagModes + t] = (double)mine;
-        if (t == 0) {
-            unsigned long long s = 0;
-            for (int w = 0; w < (T >> 5); w++) s += cqw[w];
-            cd.cq = s;
+    for (int i = 0; i < 2 * PIC_NMODES; i++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) md[i] += __shfl_down_sync(kFull, md[i], o);
+    if (lane == 0) {
+        shd[w] = fe;
+#pragma unroll
+        for (int i = 0; i < 2 * PIC_NMODES; i++) shf[i][w] = md[i];
+        cqw[w] = cqb;
+    }
+    __syncthreads();
+    if (w == 0) {
+        double sf = lane < nw ? shd[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            if (o >= nw) continue;                // warp-uniform
+            const double u = __shfl_down_sync(kFull, sf, o);
+            if (lane < o) sf += u;
+        }
+        if (lane < 2 * PIC_NMODES) {
+            float sm = 0.0f;
+            for (int j = 0; j < nw; j++) sm += shf[lane][j];
+            cd.diag[kDiagModes + lane] = (double)sm;
+        }
+        if (lane == 0) {
+            unsigned long long sc = 0;
+            for (int j = 0; j < nw; j++) sc += cqw[j];
+            cd.cq = sc;
             cd.kv[0] = kv[0];
             cd.kv[1] = kv[1];
-            cd.diag[kDiagFE] = fe;
+            cd.diag[kDiagFE] = sf;
             cd.diag[kDiagKE] = 0.0;
             cd.diag[kDiagMom] = 0.0;
             cd.diag[kDiagCharge] = charge;
@@ -232,24 +256,40 @@ __device__ void cluster_finish(const SolveArgs &a, cg::cluster_group &cl, Cluste
     }
     cl.sync();
     if (r == 0) {
-        // field f summed over the blocks in rank order by thread f
         __shared__ double tot[kDiagFields + 2];
         __shared__ unsigned long long tot_cq;
-        if (t < kDiagFields + 2) {
-            double part[kMaxSolveCluster];
+        // value f = u / 8 (f < kDiagFields + 2: a float64 field; f =
+        // kDiagFields + 2: the integer charge) from blocks 2k and 2k + 1,
+        // k = u mod 8, then a fixed butterfly over the value's 8 lanes: the
+        // remote reads are in flight together and the float64 sum is three
+        // levels deep.  u = t, t + T, ... (the trip count depends on the
+        // block size only, so every lane takes part in the shuffles).
+        static_assert(kMaxSolveCluster == 16, "8 lanes x 2 blocks per value");
+        constexpr int kSlots = (kDiagFields + 3) * 8;
+        for (int base = 0; base < kSlots; base += (int)blockDim.x) {
+            const int u = base + t, f = u >> 3, k = u & 7;
+            const bool isq = f == kDiagFields + 2;
+            const bool act = f < kDiagFields + 3;
+            const int fd = act && !isq ? f : 0;
+            double sv = 0.0;
+            unsigned long long sq = 0ull;
 #pragma unroll
-            for (int b = 0; b < kMaxSolveCluster; b++) {
+            for (int h = 0; h < 2; h++) {
+                const int b = 2 * k + h;
                 const ClusterDiag *pe = cl.map_shared_rank(&cd, b < C ? b : 0);
-                part[b] = b >= C ? 0.0 : (t < kDiagFields ? pe->diag[t] : pe->kv[t - kDiagFields]);
+                const bool use = act && b < C;
+                sv += (use && !isq) ? (fd < kDiagFields ? pe->diag[fd] : pe->kv[fd - kDiagFields]) : 0.0;
+                sq += (use && isq) ? pe->cq : 0ull;
             }
-            double acc = 0.0;
 #pragma unroll
-            for (int b = 0; b < kMaxSolveCluster; b++) acc += part[b];
-            tot[t] = acc;
-        } else if (t == kDiagFields + 2) {
-            unsigned long long acc = 0;
-            for (int b = 0; b < C; b++) acc += cl.map_shared_rank(&cd, b)->cq;
-            tot_cq = acc;
+            for (int o = 1; o < 8; o <<= 1) {
+                sv += __shfl_xor_sync(kFull, sv, o);
+                sq += __shfl_xor_sync(kFull, sq, o);
+            }
+            if (act && k == 0) {
+                if (isq) tot_cq = sq;
+                else tot[f] = sv;
+            }
         }
         __syncthreads();
         const long long n = a.npartials > 0 ? step + 1 : step;
@@ -269,9 +309,11 @@ __device__ void cluster_finish(const SolveArgs &a, cg::cluster_group &cl, Cluste
             row->charge = tot[kDiagCharge];
             row->charge_q = (long long)tot_cq;
         }
-        if (t < PIC_NMODES) {
-            const double re = tot[kDiagModes + 2 * t], im = tot[kDiagModes + 2 * t + 1];
-            row->mode[t] = 2.0 * sqrt(re * re + im * im) / (double)a.ng;
+        // the amplitudes on warp 1 (when there is one), beside thread 0's row
+        const int mt = blockDim.x >= 64 ? t - 32 : t;
+        if (mt >= 0 && mt < PIC_NMODES) {
+            const double re = tot[kDiagModes + 2 * mt], im = tot[kDiagModes + 2 * mt + 1];
+            row->mode[mt] = sqrt(re * re + im * im) * a.k_mode;
         }
     }
     cl.sync();
@@ -295,6 +337,8 @@ struct SliceSums {
 
 __global__ void __launch_bounds__(kClusterSolveThreads) pic_solve_cluster_kernel(SolveArgs a) {
     cg::cluster_group cl = cg::this_cluster();
+    pdl_wait();                                  // the push's density and sums
+    pdl_trigger();
     __shared__ SliceSums ex;
     __shared__ ClusterDiag cd;
     __shared__ i128 sh[96];
@@ -414,6 +458,8 @@ __device__ __forceinline__ double warp_div(double num, double den) {
 
 __global__ void __launch_bounds__(kClusterSolveThreads) pic_solve_cg_kernel(SolveArgs a) {
     cg::cluster_group cl = cg::this_cluster();
+    pdl_wait();                                  // the push's density and sums
+    pdl_trigger();
     __shared__ double sv[kClusterSolveThreads + 2];   // v of the slice, ghost-padded
     __shared__ CgExchange ex;
     __shared__ ClusterDiag cd;
@@ -672,7 +718,7 @@ cudaError_t launch_solve(const SolveArgs &a, cudaStream_t s) {
         solve_cluster_shape(a.ng, a.solver == PIC_SOLVER_CG ? 32 : kSolveNodesPerBlock, &C,
                             &threads);
         cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute attr[1];
+        cudaLaunchAttribute attr[2];
         cfg.gridDim = dim3((unsigned)C, 1, 1);
         cfg.blockDim = dim3((unsigned)threads, 1, 1);
         cfg.dynamicSmemBytes = 0;
@@ -681,8 +727,10 @@ cudaError_t launch_solve(const SolveArgs &a, cudaStream_t s) {
         attr[0].val.clusterDim.x = (unsigned)C;
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
+        attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[1].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = attr;
-        cfg.numAttrs = 1;
+        cfg.numAttrs = 2;
         if (a.solver == PIC_SOLVER_CG) return cudaLaunchKernelEx(&cfg, pic_solve_cg_kernel, a);
         return cudaLaunchKernelEx(&cfg, pic_solve_cluster_kernel, a);
     }

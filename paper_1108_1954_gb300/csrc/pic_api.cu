@@ -235,6 +235,7 @@ cudaError_t enqueue_solve(pic_run *r, cudaStream_t s, bool after_push) {
     a.k_rho = r->k_rho;
     a.k_e = r->k_e;
     a.k_phi = r->k_phi;
+    a.k_mode = 2.0 / (double)r->p.ncell;
     a.dx = r->dx;
     a.mass = r->mass;
     a.solver = r->p.field_solver;
