@@ -56,7 +56,7 @@ struct Exchange {
 template <int VARIANT>
 __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_group &cl,
                           Exchange &ex, Tile &tile, float *sE, i128 *sh128, double *shd,
-                          float *shf, double *kvtot) {
+                          float *shf) {
     __shared__ i128 wlast[32];
     __shared__ i128 pre[4];
     const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
@@ -83,6 +83,63 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
     float4 *x4 = reinterpret_cast<float4 *>(R.x);
     float4 *v4 = reinterpret_cast<float4 *>(R.v);
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+
+    // Block 0: the history rows of step s from the blocks' slice
+    // diagnostics.  Value f over the blocks: lane k of the value's 8 lanes
+    // reads block k, then a fixed butterfly over the lanes (f < kDiagFields:
+    // a slice diagnostic; kDiagFields, +1: the push sums; kDiagFields + 2:
+    // the integer charge); thread 0 writes the scalars and warp 1 the mode
+    // amplitudes.  Called for step s just before the next step's first
+    // cluster barrier (where block 0 would wait for its peers anyway), or
+    // after the last step: the peers rewrite their slice diagnostics only
+    // after that barrier, and stay resident until block 0 has passed it.
+    __shared__ double tot[kDiagFields + 2];
+    __shared__ unsigned long long cqt;
+    auto write_rows = [&](int s) {
+        static_assert(kMaxCluster == 8, "8 lanes per value");
+        constexpr int kSlots = (kDiagFields + 3) * 8;
+        for (int base = 0; base < kSlots; base += bs) {
+            const int u = base + tid, f = u >> 3, k = u & 7;
+            const bool isq = f == kDiagFields + 2;
+            const bool use = f < kDiagFields + 3 && k < C;
+            const int fd = f < kDiagFields + 2 ? f : 0;
+            const Exchange *pe = cl.map_shared_rank(&ex, k < C ? k : 0);
+            double sv = (use && !isq) ? (fd < kDiagFields ? pe->diag[fd] : pe->kv[fd - kDiagFields]) : 0.0;
+            unsigned long long sq = (use && isq) ? pe->cq : 0ull;
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                sv += __shfl_xor_sync(kFull, sv, o);
+                sq += __shfl_xor_sync(kFull, sq, o);
+            }
+            if (f < kDiagFields + 3 && k == 0) {
+                if (isq) cqt = sq;
+                else tot[f] = sv;
+            }
+        }
+        __syncthreads();                          // block 0 only
+        const long long n = push ? step0 + s + 1 : step0 + s;
+        pic_diag_row *row = &R.hist[n % R.hist_len];
+        if (tid == 0) {
+            if (push) {
+                pic_diag_row *prev = &R.hist[(step0 + s) % R.hist_len];
+                prev->kinetic = 0.5 * R.mass * tot[kDiagFields];
+                prev->momentum = R.mass * tot[kDiagFields + 1];
+            }
+            const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+            row->step = n;
+            row->kinetic = qnan;
+            row->momentum = qnan;
+            row->field = 0.5 * R.dx * tot[kDiagFE];
+            row->charge = tot[kDiagCharge];
+            row->charge_q = (long long)cqt;
+        }
+        const int mt = bs >= 64 ? tid - 32 : tid;
+        if (mt >= 0 && mt < PIC_NMODES) {
+            const double re = tot[kDiagModes + 2 * mt], im = tot[kDiagModes + 2 * mt + 1];
+            row->mode[mt] = sqrt(re * re + im * im) * R.k_mode;
+        }
+        __syncthreads();                          // tot and cqt free again
+    };
 
     for (int s = 0; s < steps; s++) {
         const bool last = s == steps - 1;
@@ -135,24 +192,10 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
             deposit_one<VARIANT>(tile, xs, valid, c, a.err, lane);
             if (push && valid) { R.x[i] = xs; R.v[i] = vs; }
         }
-        {
-            double kv[2] = {(double)ke, (double)mom};
-            block_sum_f64k<2>(kv, shd);
-            if (tid == 0) { ex.kv[0] = kv[0]; ex.kv[1] = kv[1]; }
-        }
+        if (r == 0 && s > 0) write_rows(s - 1);     // the previous step's rows
         cl.sync();                                                    // #1
 
         // ---- B: node slice sums over the cluster's tiles
-        if (r == 0 && tid < 2) {
-            double part[kMaxCluster];
-#pragma unroll
-            for (int b = 0; b < kMaxCluster; b++)
-                part[b] = b < C ? cl.map_shared_rank(&ex, b)->kv[tid] : 0.0;
-            double k = 0.0;
-#pragma unroll
-            for (int b = 0; b < kMaxCluster; b++) k += part[b];
-            kvtot[tid] = k;
-        }
         // one node per thread: g = b0 + tid (the pool keeps ceil(NG/C) <= block)
         const int g = b0 + tid;
         const bool mine = g < b1;
@@ -170,14 +213,21 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
                 rq += ((unsigned long long)hi[b] << 32) | lo[b];
             // the ghost words: index 0 (node -1) folds onto node NG-1, index
             // NG+1 (node NG) onto node 0
-            if (g == ng - 1)
-                for (int b = 0; b < C; b++)
-                    rq += ((unsigned long long)cl.map_shared_rank(tile.hi, b)[0] << 32) |
-                          cl.map_shared_rank(tile.lo, b)[0];
-            if (g == 0)
-                for (int b = 0; b < C; b++)
-                    rq += ((unsigned long long)cl.map_shared_rank(tile.hi, b)[ng + 1] << 32) |
-                          cl.map_shared_rank(tile.lo, b)[ng + 1];
+            // (both for NG = 1), the blocks' words read together
+            for (int side = 0; side < 2; side++) {
+                const bool fold = side == 0 ? g == ng - 1 : g == 0;
+                if (!fold) continue;
+                const int jg = side == 0 ? 0 : ng + 1;
+                unsigned glo[kMaxCluster], ghi[kMaxCluster];
+#pragma unroll
+                for (int b = 0; b < kMaxCluster; b++) {
+                    glo[b] = b < C ? cl.map_shared_rank(tile.lo, b)[jg] : 0u;
+                    ghi[b] = b < C ? cl.map_shared_rank(tile.hi, b)[jg] : 0u;
+                }
+#pragma unroll
+                for (int b = 0; b < kMaxCluster; b++)
+                    rq += ((unsigned long long)ghi[b] << 32) | glo[b];
+            }
         }
         const i128 Rg = mine ? (i128)ntot - (i128)ng * (i128)rq : (i128)0;
         {
@@ -239,40 +289,66 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
             }
             node_diag(d, g, ng, E, E32);
         }
-        const unsigned long long cq = rq;
+        // the block's sums of the field energy (float64), the push sums and
+        // the mode sums (float32 within a warp) and the integer charge, with
+        // one barrier.  Warp sums by shuffles: the field energy by the
+        // predicated float64 tree, the mode sums by recursive halving.  Then,
+        // beside each other, warp 0 adds the mode sums over the warps (one
+        // lane per value, warp order) and warp 1 the other values (one lane
+        // each, float64, warp order).  GB300's float64 pipe takes 2 lanes per
+        // clock, so the float64 work stays at one tree per warp.
         {
-            double dv[1] = {d.fe};
-            block_sum_f64k<1>(dv, shd);
+            double fe = d.fe;
+            float k0 = ke, k1 = mom;
+            unsigned long long cqb = rq;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double u = __shfl_down_sync(kFull, fe, o);
+                if (lane < o) fe += u;
+                k0 += __shfl_down_sync(kFull, k0, o);
+                k1 += __shfl_down_sync(kFull, k1, o);
+                cqb += __shfl_down_sync(kFull, cqb, o);
+            }
             float md[2 * PIC_NMODES];
 #pragma unroll
             for (int m = 0; m < PIC_NMODES; m++) { md[2 * m] = d.re[m]; md[2 * m + 1] = d.im[m]; }
-            block_sum_t<2 * PIC_NMODES, float>(md, shf);
-            unsigned long long cqb = cq;
-            for (int o = 16; o > 0; o >>= 1) cqb += __shfl_down_sync(kFull, cqb, o);
+            static_assert(2 * PIC_NMODES == 16, "16 mode sums per warp");
+            const float msum = warp_sum16_halving(md, lane);   // value lane/2
+            const int w = tid >> 5, nw = bs >> 5;
             __shared__ unsigned long long cqw[32];
-            if (lane == 0) cqw[tid >> 5] = cqb;
+            if ((lane & 1) == 0) shf[(lane >> 1) * 32 + w] = msum;
+            if (lane == 0) {
+                shd[w] = fe;
+                shd[32 + w] = (double)k0;
+                shd[64 + w] = (double)k1;
+                cqw[w] = cqb;
+            }
             __syncthreads();
-            if (tid < 32) {
-                // lane m of warp 0 stores value m (md is complete in warp 0)
-                float mine = 0.0f;
-#pragma unroll
-                for (int m = 0; m < 2 * PIC_NMODES; m++) mine = (m == tid) ? md[m] : mine;
-                if (tid < 2 * PIC_NMODES) ex.diag[kDiagModes + tid] = (double)mine;
-                if (tid == 0) {
-                    unsigned long long t = 0;
-                    for (int w = 0; w < (bs >> 5); w++) t += cqw[w];
-                    ex.cq = t;
-                    ex.diag[kDiagFE] = dv[0];
-                    ex.diag[kDiagKE] = 0.0;
-                    ex.diag[kDiagMom] = 0.0;
-                    ex.diag[kDiagCharge] = r == 0 ? R.dx * R.k_rho * i128_to_f64(SR) : 0.0;
-                }
+            const int wo = nw > 1 ? 1 : 0;        // the warp of the other values
+            if (w == 0 && lane < 2 * PIC_NMODES) {
+                float sm = 0.0f;
+                for (int j = 0; j < nw; j++) sm += shf[lane * 32 + j];
+                ex.diag[kDiagModes + lane] = (double)sm;
+            }
+            if (w == wo && lane < 3) {
+                double sd = 0.0;
+                for (int j = 0; j < nw; j++) sd += shd[lane * 32 + j];
+                if (lane == 0) ex.diag[kDiagFE] = sd;
+                else ex.kv[lane - 1] = sd;
+            }
+            if (w == wo && lane == 3) {
+                unsigned long long t = 0;
+                for (int j = 0; j < nw; j++) t += cqw[j];
+                ex.cq = t;
+                ex.diag[kDiagKE] = 0.0;
+                ex.diag[kDiagMom] = 0.0;
+                ex.diag[kDiagCharge] = r == 0 ? R.dx * R.k_rho * i128_to_f64(SR) : 0.0;
             }
         }
         cl.sync();                                                    // #3
 
         // ---- C: the other slices of E into the own copy (kCopy remote
-        // loads in flight per thread); history rows
+        // loads in flight per thread)
         constexpr int kCopy = 8;
         for (int j0 = tid; j0 < ng + 2; j0 += kCopy * bs) {
             float e[kCopy];
@@ -293,57 +369,9 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
                 tile.hi[j] = 0u;
             }
         }
-        // block 0: field f of the diagnostics summed over the blocks by
-        // thread f (rank order), then one thread writes the history rows
-        __shared__ double tot[kDiagFields];
-        __shared__ unsigned long long cqt;
-        if (r == 0 && tid <= kDiagFields) {
-            if (tid < kDiagFields) {
-                double part[kMaxCluster];
-#pragma unroll
-                for (int b = 0; b < kMaxCluster; b++)
-                    part[b] = b < C ? cl.map_shared_rank(&ex, b)->diag[tid] : 0.0;
-                double acc = 0.0;
-#pragma unroll
-                for (int b = 0; b < kMaxCluster; b++) acc += part[b];
-                tot[tid] = acc;
-            } else {
-                unsigned long long part[kMaxCluster];
-#pragma unroll
-                for (int b = 0; b < kMaxCluster; b++)
-                    part[b] = b < C ? cl.map_shared_rank(&ex, b)->cq : 0ull;
-                unsigned long long acc = 0;
-#pragma unroll
-                for (int b = 0; b < kMaxCluster; b++) acc += part[b];
-                cqt = acc;
-            }
-        }
-        __syncthreads();
-        if (r == 0 && tid < 32) {
-            // scalars by thread 0, mode m by thread m
-            const long long n = push ? step0 + s + 1 : step0 + s;
-            pic_diag_row *row = &R.hist[n % R.hist_len];
-            if (tid == 0) {
-                if (push) {
-                    pic_diag_row *prev = &R.hist[(step0 + s) % R.hist_len];
-                    prev->kinetic = 0.5 * R.mass * kvtot[0];
-                    prev->momentum = R.mass * kvtot[1];
-                }
-                const double qnan = __longlong_as_double(0x7ff8000000000000ll);
-                row->step = n;
-                row->kinetic = qnan;
-                row->momentum = qnan;
-                row->field = 0.5 * R.dx * tot[kDiagFE];
-                row->charge = tot[kDiagCharge];
-                row->charge_q = (long long)cqt;
-            }
-            if (tid < PIC_NMODES) {
-                const double re = tot[kDiagModes + 2 * tid], im = tot[kDiagModes + 2 * tid + 1];
-                row->mode[tid] = 2.0 * sqrt(re * re + im * im) / (double)ng;
-            }
-        }
-        __syncthreads();
+        __syncthreads();                          // sE and the tile complete
     }
+    if (r == 0) write_rows(steps - 1);
     if (r == 0 && tid == 0 && push) *R.step = step0 + steps;
 }
 
@@ -354,9 +382,8 @@ __global__ void __launch_bounds__(512, MINB) pic_batch_kernel(BatchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Exchange ex;
     __shared__ i128 sh128[96];
-    __shared__ double shd[32 * 2];
-    __shared__ float shf[32 * 2 * PIC_NMODES];
-    __shared__ double kvtot[2];
+    __shared__ __align__(16) double shd[32 * 3];
+    __shared__ __align__(16) float shf[32 * 2 * PIC_NMODES];
     cg::cluster_group cl = cg::this_cluster();
     const int ngm = a.ng_max;
     Tile tile;
@@ -374,7 +401,7 @@ __global__ void __launch_bounds__(512, MINB) pic_batch_kernel(BatchArgs a) {
         if (ticket >= a.nrun) break;
         const BatchRun R = a.runs[a.order[ticket]];
         if (!(a.push && R.steps == 0))
-            run_steps<VARIANT>(a, R, cl, ex, tile, sE, sh128, shd, shf, kvtot);
+            run_steps<VARIANT>(a, R, cl, ex, tile, sE, sh128, shd, shf);
         cl.sync();
     }
 }

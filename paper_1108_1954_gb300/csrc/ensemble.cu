@@ -322,6 +322,7 @@ int admit_common(pic_pool *pool, const pic_params *p, int64_t steps, int32_t *sl
     d.k_rho = p->rho_ion / std::ldexp((double)p->npart, kFixBits);
     d.k_e = 0.5 * d.dx * d.k_rho / (double)p->ncell;
     d.k_phi = -d.dx * d.dx * d.k_rho / (double)p->ncell;
+    d.k_mode = 2.0 / (double)p->ncell;
     cudaError_t e = cudaMemsetAsync(d.step, 0, 8, pool->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.E32, 0, 4 * (size_t)p->ncell, pool->stream);
     if (e == cudaSuccess)

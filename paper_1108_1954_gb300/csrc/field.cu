@@ -204,9 +204,10 @@ __device__ void cluster_finish(const SolveArgs &a, cg::cluster_group &cl, Cluste
     const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
     const int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = blockDim.x >> 5;
     // The block's sums of the field energy (float64), the mode sums (float32)
-    // and the integer charge with one barrier: warp sums by shuffles, then
-    // warp 0 across the warps -- the field energy by the predicated float64
-    // tree, each mode sum by one lane in warp order.
+    // and the integer charge with one barrier: warp sums by shuffles (the 16
+    // mode sums by recursive halving), then warp 0 across the warps -- the
+    // field energy by the predicated float64 tree, each mode sum by one lane
+    // in warp order.
     double fe = d.fe;
     unsigned long long cqb = q;
 #pragma unroll
@@ -218,14 +219,11 @@ __device__ void cluster_finish(const SolveArgs &a, cg::cluster_group &cl, Cluste
     float md[2 * PIC_NMODES];
 #pragma unroll
     for (int m = 0; m < PIC_NMODES; m++) { md[2 * m] = d.re[m]; md[2 * m + 1] = d.im[m]; }
-#pragma unroll
-    for (int i = 0; i < 2 * PIC_NMODES; i++)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) md[i] += __shfl_down_sync(kFull, md[i], o);
+    static_assert(2 * PIC_NMODES == 16, "16 mode sums per warp");
+    const float msum = warp_sum16_halving(md, lane);   // value lane/2 in lanes 2i, 2i+1
+    if ((lane & 1) == 0) shf[lane >> 1][w] = msum;
     if (lane == 0) {
         shd[w] = fe;
-#pragma unroll
-        for (int i = 0; i < 2 * PIC_NMODES; i++) shf[i][w] = md[i];
         cqw[w] = cqb;
     }
     __syncthreads();

@@ -75,6 +75,40 @@ static __device__ void block_sum3_i128(i128 &a, i128 &b, i128 &c, i128 *sh /*[96
 // sum of each value by warp 0: for float64 (a slow pipe on GB300, so the
 // dependent chain matters) a butterfly over the warp sums, one value at a
 // time; for float32 lane i adds value i over the warps.
+// Sums of 16 float32 values over the 32 lanes of a warp by recursive
+// halving: at offset o = 16, 8, 4, 2 a lane keeps the half of its values
+// that bit o of its lane index selects, adds the partner's (lane ^ o) copy
+// of that half, and sends it the other half; a last exchange at offset 1
+// completes the sums.  Lanes 2i and 2i+1 return the warp sum of value i.
+// 16 shuffles instead of the 80 of 16 separate trees; the order of the
+// additions is fixed.
+__device__ __forceinline__ float warp_sum16_halving(const float (&v)[16], int lane) {
+    float h8[8], h4[4], h2[2];
+    const bool b16 = lane & 16, b8 = lane & 8, b4 = lane & 4, b2 = lane & 2;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        const float send = b16 ? v[i] : v[i + 8];
+        const float keep = b16 ? v[i + 8] : v[i];
+        h8[i] = keep + __shfl_xor_sync(kFull, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const float send = b8 ? h8[i] : h8[i + 4];
+        const float keep = b8 ? h8[i + 4] : h8[i];
+        h4[i] = keep + __shfl_xor_sync(kFull, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        const float send = b4 ? h4[i] : h4[i + 2];
+        const float keep = b4 ? h4[i + 2] : h4[i];
+        h2[i] = keep + __shfl_xor_sync(kFull, send, 4);
+    }
+    const float send = b2 ? h2[0] : h2[1];
+    const float keep = b2 ? h2[1] : h2[0];
+    const float h1 = keep + __shfl_xor_sync(kFull, send, 2);
+    return h1 + __shfl_xor_sync(kFull, h1, 1);
+}
+
 template <int K, typename T>
 static __device__ void block_sum_t(T (&v)[K], T *sh /*[32*K]*/) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;

@@ -149,6 +149,7 @@ struct BatchRun {
     long long *step;              // device step counter of the run
     long long weight_total;       // N 2^24
     double k_rho, k_e, k_phi, dx, mass;
+    double k_mode;                // 2 / NG: mode amplitude of the mode sums
 };
 
 struct BatchArgs {
