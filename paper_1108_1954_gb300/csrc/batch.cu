@@ -57,8 +57,8 @@ template <int VARIANT>
 __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_group &cl,
                           Exchange &ex, Tile &tile, float *sE, i128 *sh128, double *shd,
                           float *shf) {
-    __shared__ i128 wlast[32];
     __shared__ i128 pre[4];
+    __shared__ __align__(16) unsigned long long scan64[4 * 32];
     const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
     const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31;
     const PushConsts c = R.pc;
@@ -258,19 +258,12 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
         __syncthreads();
         const i128 A0 = pre[0], B = pre[1], SR = pre[2], SS1 = pre[3];
         const i128 SP = (i128)ng * SR - SS1;          // sum_k (NG-k) R_k
-        const i128 A1 = (i128)b0 * A0 - B;             // sum_{k<b0} (b0-k) R_k
-        i128 tot_;
-        const i128 Pg = A0 + block_inclusive_scan_i128(Rg, sh128, tot_);      // P_g
-        const i128 Pin = mine ? Pg : (i128)0;
-        const i128 pex = block_inclusive_scan_i128(Pin, sh128, tot_) - Pin;  // sum_{b0<=k<g} P_k
+        // one pass of the slice's inclusive scans of R_k and k R_k
+        const I128Pair sc = block_inclusive_scan2_i128(Rg, Rg * (i128)g, scan64);
+        const i128 Pg = A0 + sc.a;                                          // P_g
         const i128 M = (i128)ng * Pg - SP;                                  // M_g
-        // M_{g-1}: previous thread, or the slice's left neighbour for tid 0
-        i128 Mprev = shfl_up_i128(M, 1);
-        if (lane == 31) wlast[tid >> 5] = M;
-        __syncthreads();
-        if (lane == 0)
-            Mprev = tid == 0 ? (b0 == 0 ? (i128)ng * SR - SP : (i128)ng * A0 - SP)
-                             : wlast[(tid >> 5) - 1];
+        // M_{g-1} = NG P_{g-1} - SP with P_{g-1} = P_g - R_g; M_{-1} = M_{NG-1}
+        const i128 Mprev = g == 0 ? (i128)ng * SR - SP : (i128)ng * (Pg - Rg) - SP;
         NodeDiag d;
         node_diag_reset(d);
         if (mine) {
@@ -280,7 +273,9 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
             if (g == ng - 1) sE[0] = E32;
             if (g == 0) sE[ng + 1] = E32;
             if (last) {
-                const i128 sumM = (i128)ng * (A1 + pex) - (i128)g * SP;
+                // sum_{k<g} P_k = sum_{j<g} (g - j) R_j = g P_g - sum_{j<=g} j R_j
+                const i128 sumP = (i128)g * Pg - (B + sc.b);
+                const i128 sumM = (i128)ng * sumP - (i128)g * SP;         // sum_{k<g} M_k
                 R.E64[g] = E;
                 R.E32[g] = E32;
                 R.phi[g] = R.k_phi * i128_to_f64(sumM);

@@ -340,10 +340,10 @@ __global__ void __launch_bounds__(kClusterSolveThreads) pic_solve_cluster_kernel
     __shared__ SliceSums ex;
     __shared__ ClusterDiag cd;
     __shared__ i128 sh[96];
-    __shared__ i128 wlast[32];
     __shared__ i128 pre[4];
+    __shared__ __align__(16) unsigned long long scan64[4 * 32];
     const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
-    const int ng = a.ng, t = threadIdx.x, lane = t & 31;
+    const int ng = a.ng, t = threadIdx.x;
     const long long step = *a.dstep;
     const long long ntot = a.weight_total;
     const int per = (ng + C - 1) / C;
@@ -386,22 +386,18 @@ __global__ void __launch_bounds__(kClusterSolveThreads) pic_solve_cluster_kernel
     __syncthreads();
     const i128 A0 = pre[0], B = pre[1], SR = pre[2], SS1 = pre[3];
     const i128 SP = (i128)ng * SR - SS1;          // sum_k (NG-k) R_k
-    const i128 A1 = (i128)b0 * A0 - B;             // sum_{k<b0} (b0-k) R_k
-    i128 tot_;
-    const i128 P = A0 + block_inclusive_scan_i128(R, sh, tot_);        // P_g
-    const i128 Pin = mine ? P : (i128)0;
-    const i128 pex = block_inclusive_scan_i128(Pin, sh, tot_) - Pin;    // sum_{b0<=k<g} P_k
+    // one pass of the slice's inclusive scans of R_k and k R_k
+    const I128Pair sc = block_inclusive_scan2_i128(R, R * (i128)g, scan64);
+    const i128 P = A0 + sc.a;                                          // P_g
     const i128 M = (i128)ng * P - SP;                                  // M_g
-    i128 Mprev = shfl_up_i128(M, 1);
-    if (lane == 31) wlast[t >> 5] = M;
-    __syncthreads();
-    if (lane == 0)
-        Mprev = t == 0 ? (b0 == 0 ? (i128)ng * SR - SP : (i128)ng * A0 - SP)
-                       : wlast[(t >> 5) - 1];
+    // M_{g-1} = NG P_{g-1} - SP with P_{g-1} = P_g - R_g; M_{-1} = M_{NG-1}
+    const i128 Mprev = g == 0 ? (i128)ng * SR - SP : (i128)ng * (P - R) - SP;
     NodeDiag d;
     node_diag_reset(d);
     if (mine) {
-        const i128 sumM = (i128)ng * (A1 + pex) - (i128)g * SP;
+        // sum_{k<g} P_k = sum_{j<g} (g - j) R_j = g P_g - sum_{j<=g} j R_j
+        const i128 sumP = (i128)g * P - (B + sc.b);
+        const i128 sumM = (i128)ng * sumP - (i128)g * SP;                // sum_{k<g} M_k
         const double E = a.k_e * i128_to_f64(M + Mprev);
         const float E32 = (float)E;
         a.rho[g] = a.k_rho * i128_to_f64(R);

@@ -55,6 +55,42 @@ static __device__ i128 block_inclusive_scan_i128(i128 v, i128 *sh, i128 &total) 
     return v + off;
 }
 
+// Inclusive scans of two i128 values per thread over the block, in one
+// pass with one barrier.  The warp totals go through shared memory as
+// 64-bit halves (w64: 4 x 32 words), so every shared access is 8 bytes.  No
+// trailing barrier: a caller that writes w64 again must synchronise first.
+struct I128Pair {
+    i128 a, b;
+};
+__device__ __forceinline__ I128Pair block_inclusive_scan2_i128(i128 a, i128 b,
+                                                               unsigned long long *w64) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const i128 ta = shfl_up_i128(a, o), tb = shfl_up_i128(b, o);
+        if (lane >= o) {
+            a += ta;
+            b += tb;
+        }
+    }
+    if (lane == 31) {
+        w64[w] = (unsigned long long)a;
+        w64[32 + w] = (unsigned long long)(a >> 64);
+        w64[64 + w] = (unsigned long long)b;
+        w64[96 + w] = (unsigned long long)(b >> 64);
+    }
+    __syncthreads();
+    i128 oa = 0, ob = 0;
+    for (int i = 0; i < w; i++) {
+        oa += (i128)(((unsigned __int128)w64[32 + i] << 64) | w64[i]);
+        ob += (i128)(((unsigned __int128)w64[96 + i] << 64) | w64[64 + i]);
+    }
+    I128Pair r;
+    r.a = a + oa;
+    r.b = b + ob;
+    return r;
+}
+
 // Sum of three i128 values over the block (all threads get the sums).
 static __device__ void block_sum3_i128(i128 &a, i128 &b, i128 &c, i128 *sh /*[96]*/) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
