@@ -235,8 +235,11 @@ def time_ours(args, w, x32, v32):
     torch.cuda.synchronize()
     K = args.steps
     # the step loop through the public API: pic_step_n replays CUDA graphs of
-    # whole sort periods (the graphs are captured on the first call)
-    run.step_n(2 * S if S > 0 else 32)
+    # whole sort periods, one per buffer parity, each captured the first time
+    # a sort point is reached with a whole period to go; three periods from
+    # here pass two such sort points, so both graphs exist before the timed
+    # region
+    run.step_n(3 * S if S > 0 else 32)
     torch.cuda.synchronize()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = Clocks(torch.cuda.current_device())
@@ -314,8 +317,10 @@ def time_e2e(args, w, x32, v32):
     run.init(xh, vh)                      # warm: autotune, graph capture, first touch
     run.step_n(w["sort_interval"] + 1)
     if not args.no_tune and not args.variant:
-        run.autotune(reps=8)
-    run.step_n(w["sort_interval"] + 1)
+        run.autotune(reps=8)              # (drops the captured graphs)
+    # three sort periods pass two sort points with a whole period to go:
+    # both buffer parities' graphs are captured before the timed region
+    run.step_n(3 * w["sort_interval"] if w["sort_interval"] > 0 else 32)
     run.sync()
     torch.cuda.synchronize()
     t = time.perf_counter()
