@@ -538,7 +538,9 @@ def time_c1(args):
     """Config 1 (20,000 electrons, 64 cells, 200 steps): launch-bound, so
     reported as microseconds per step -- through pic_step_n (CUDA graphs of
     16 steps) and as a one-run pool (all 200 steps in one cluster launch; the
-    fastest of clusters of 1, 2, 4 and 8 blocks)."""
+    fastest of clusters of 1, 2, 4 and 8 blocks); and in the configuration's
+    own float64 precision through pic_step_n."""
+    import numpy as np
     import torch
     import workloads as W
     import paper_1108_1954_gb300 as pic
@@ -556,6 +558,20 @@ def time_c1(args):
     e1.record(s)
     torch.cuda.synchronize()
     t_graph = e0.elapsed_time(e1) / 1e3
+    run.close()
+    # the configuration's own precision: float64 push, deposit and solve
+    run = pic.Run(pic.Params(npart=n, ncell=ng, length=L, dt=0.1, history=K + 1,
+                             precision=pic.PIC_FP64))
+    x64, v64 = x.astype(np.float64), v.astype(np.float64)
+    run.init(x64, v64)
+    run.step_n(32)
+    run.init(x64, v64)
+    s = run.stream
+    e0.record(s)
+    run.step_n(K)
+    e1.record(s)
+    torch.cuda.synchronize()
+    t_fp64 = e0.elapsed_time(e1) / 1e3
     run.close()
     best = None
     for cluster in (1, 2, 4, 8):
@@ -577,6 +593,7 @@ def time_c1(args):
     t_pool, cluster = best
     return {"npart": n, "ncell": ng, "steps": K,
             "us_per_step_graphs": 1e6 * t_graph / K, "us_per_step_one_launch": 1e6 * t_pool / K,
+            "us_per_step_graphs_fp64": 1e6 * t_fp64 / K,
             "one_launch_shape": {"variant": 5, "cluster": cluster, "block": 256},
             "value_graphs": n * K / t_graph, "value_one_launch": n * K / t_pool,
             "unit": "particle-steps/s"}

@@ -138,11 +138,14 @@ __device__ void finalize(const SolveArgs &a, long long step) {
         row->field = 0.5 * a.dx * tot[kDiagFE];
         row->charge = tot[kDiagCharge];
         row->charge_q = (long long)tot_cq;
-        for (int m = 0; m < PIC_NMODES; m++) {
-            const double re = tot[kDiagModes + 2 * m], im = tot[kDiagModes + 2 * m + 1];
-            row->mode[m] = 2.0 * sqrt(re * re + im * im) / (double)ng;
-        }
         *a.counter = 0u;
+    }
+    // the mode amplitudes one lane each (warp 1 when there is one)
+    const int mt = blockDim.x >= 64 ? (int)threadIdx.x - 32 : (int)threadIdx.x;
+    if (mt >= 0 && mt < PIC_NMODES) {
+        const long long n = a.npartials > 0 ? step + 1 : step;
+        const double re = tot[kDiagModes + 2 * mt], im = tot[kDiagModes + 2 * mt + 1];
+        a.hist[n % a.hist_len].mode[mt] = sqrt(re * re + im * im) * a.k_mode;
     }
 }
 
@@ -728,7 +731,10 @@ cudaError_t launch_solve(const SolveArgs &a, cudaStream_t s) {
         if (a.solver == PIC_SOLVER_CG) return cudaLaunchKernelEx(&cfg, pic_solve_cg_kernel, a);
         return cudaLaunchKernelEx(&cfg, pic_solve_cluster_kernel, a);
     }
-    pic_solve_float_kernel<<<1, kSolveThreads, 0, s>>>(a);
+    // one block, one warp per 32 nodes up to kSolveThreads (the float64
+    // scans cost per warp, not per node)
+    const int threads = a.ng >= kSolveThreads ? kSolveThreads : ((a.ng + 31) / 32) * 32;
+    pic_solve_float_kernel<<<1, threads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
