@@ -19,8 +19,8 @@
 //      E (Eq. 7 via the flux form of Eq. 6) for its slice in 128-bit integers,
 //      float64 at the last conversion; cluster barrier;
 //   C  each block copies the other slices of E into its own shared copy;
-//      block 0 reduces the slice diagnostics in rank order and writes the
-//      history rows.
+//      block 0 sums the slice diagnostics over the blocks and writes the
+//      step's history rows just before the next step's first barrier.
 //
 // A slice has at most one node per thread (ceil(NG/C) <= block, checked by
 // the pool), so the integer solve of a slice is one block-wide scan.

@@ -26,10 +26,11 @@
 // shared memory, and block 0 reduces the diagnostics and writes the history
 // rows.
 //
-// Float modes (precision study): one block, float64 prefix scans of rho; the
-// block then reduces the diagnostics, writes the history rows, clears the
-// density accumulator and advances the step counter (finalize).  The paper's
-// CG solver (PIC_SOLVER_CG) runs the same way in one block.
+// Float modes (precision study): one block (one warp per 32 nodes, at most
+// kSolveThreads threads), float64 prefix scans of rho; the block then reduces
+// the diagnostics, writes the history rows, clears the density accumulator
+// and advances the step counter (finalize).  The paper's CG solver
+// (PIC_SOLVER_CG) runs on a thread-block cluster (below).
 //
 // Diagnostics: field energy (1/2) dx sum E^2 in float64; mode amplitudes
 // from the float32 field with float32 twiddles, summed per block in float32
@@ -328,10 +329,13 @@ __device__ void cluster_finish(const SolveArgs &a, cg::cluster_group &cl, Cluste
 // publishes its slice sums sum_k R_k and sum_k k R_k in shared memory.  After
 // a cluster barrier every block forms, from all slices' sums (one remote read
 // per lane of warp 0; integer sums, so the order does not matter),
-//   A0 = sum_{k<b0} R_k,  A1 = b0 A0 - sum_{k<b0} k R_k,
+//   A0 = sum_{k<b0} R_k,  B = sum_{k<b0} k R_k,
 //   SR = sum_k R_k,       SP = NG SR - sum_k k R_k,
-// and solves its slice with two block-wide scans as above; then the
-// diagnostics (cluster_finish).  Three cluster barriers, no global atomics.
+// and solves its slice with one block pass of two inclusive scans, of R_k and
+// of k R_k (I and J below, over b0 <= k <= g): P_g = A0 + I, M_g = NG P_g - SP,
+// M_{g-1} = NG (P_g - R_g) - SP (M_{-1} = NG SR - SP), and
+// sum_{k<g} P_k = g P_g - (B + J); then the diagnostics (cluster_finish).
+// Three cluster barriers, no global atomics.
 struct SliceSums {
     i128 s0, s1;                  // slice sums of R and k R
 };

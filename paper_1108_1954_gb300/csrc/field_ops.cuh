@@ -35,26 +35,6 @@ __device__ __forceinline__ double i128_to_f64(i128 v) {
 }
 
 
-// Inclusive scan of one i128 per thread over the block; returns the inclusive
-// value and the block total.  sh must hold 33 entries.
-static __device__ i128 block_inclusive_scan_i128(i128 v, i128 *sh, i128 &total) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int o = 1; o < 32; o <<= 1) {
-        const i128 t = shfl_up_i128(v, o);
-        if (lane >= o) v += t;
-    }
-    if (lane == 31) sh[w] = v;
-    __syncthreads();
-    i128 off = 0, tot = 0;
-    for (int i = 0; i < nw; i++) {
-        if (i < w) off += sh[i];
-        tot += sh[i];
-    }
-    __syncthreads();
-    total = tot;
-    return v + off;
-}
-
 // Inclusive scans of two i128 values per thread over the block, in one
 // pass with one barrier.  The warp totals go through shared memory as
 // 64-bit halves (w64: 4 x 32 words), so every shared access is 8 bytes.  No
