@@ -20,8 +20,11 @@ def periodic_dist(a, b, L):
     return np.minimum(d, L - d)
 
 
-@pytest.mark.parametrize("n,ng", [(20000, 64), (100003, 1024)])
+@pytest.mark.parametrize("n,ng", [(20000, 64), (20001, 100), (100003, 1024), (100003, 3000),
+                                  (200001, 8192), (7, 1)])
 def test_fp64_mode_one_step(n, ng):
+    # the float64 solve's block has one warp per 32 nodes up to 1024 threads:
+    # NG = 100 ends mid-warp, 3000 and 8192 give each thread several nodes
     x, v = W.two_stream(n, L4PI, 0.2, 0.02, 7 + n)
     run = pic.Run(pic.Params(npart=n, ncell=ng, length=L4PI, precision=pic.PIC_FP64),
                   device="cuda:0")
