@@ -90,7 +90,7 @@ __device__ __forceinline__ void block_sum2(double &a, double &b, double *scratch
 // iteration's groups are loaded before the current ones are processed.
 template <int VARIANT, bool PUSH, int U>
 __global__ void __launch_bounds__(512) pic_push_fixed_kernel(PushArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double red[64];
     pdl_wait();                                  // E, x, v and rho_q of the kernel before
     pdl_trigger();
@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(kBulkThreads) pic_push_bulk_kernel(PushArgs a)
 
 template <bool PUSH>
 __global__ void __launch_bounds__(1024) pic_push_f32atomic_kernel(PushArgsF32Atomic a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double red[64];
     const PushConsts c = a.c;
     const int ng = c.ng;
@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(1024) pic_push_f32atomic_kernel(PushArgsF32Ato
 
 template <bool PUSH>
 __global__ void __launch_bounds__(1024) pic_push_f64_kernel(PushArgs64 a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double red[64];
     double *sRho = reinterpret_cast<double *>(smem_raw);
     double *sE = sRho + a.ng;
@@ -449,12 +449,17 @@ __global__ void __launch_bounds__(1024) pic_push_f64_kernel(PushArgs64 a) {
     __syncthreads();
     double ke = 0.0, mom = 0.0;
     const long long stride = (long long)gridDim.x * bs;
-    for (long long i = (long long)blockIdx.x * bs + tid; i < a.n; i += stride) {
-        double x = a.x[i];
+    const int lane = tid & 31;
+    // the trip count is uniform over a warp (base is), so every lane takes
+    // part in the deposit's shuffles
+    for (long long base = (long long)blockIdx.x * bs + (tid & ~31); base < a.n; base += stride) {
+        const long long i = base + lane;
+        const bool valid = i < a.n;
+        double x = valid ? a.x[i] : 0.0;
         double s = x * a.inv_dx - 0.5;
         double fl = floor(s);
-        bool ok = fl >= -1.0 && fl <= (double)(ng - 1);
-        if (PUSH) {
+        bool ok = valid && fl >= -1.0 && fl <= (double)(ng - 1);
+        if (PUSH && valid) {
             double v = a.v[i];
             int j = ok ? (int)fl : 0;
             int il = j < 0 ? j + ng : j, ir = j + 1 >= ng ? j + 1 - ng : j + 1;
@@ -473,15 +478,35 @@ __global__ void __launch_bounds__(1024) pic_push_f64_kernel(PushArgs64 a) {
             fl = floor(s);
             ok = fl >= -1.0 && fl <= (double)(ng - 1);
         }
-        if (ok) {
-            int j = (int)fl;
-            int il = j < 0 ? j + ng : j, ir = j + 1 >= ng ? j + 1 - ng : j + 1;
-            double f = s - fl;
-            atomicAdd(&sRho[il], 1.0 - f);
-            atomicAdd(&sRho[ir], f);
-        } else {
-            atomicOr(a.err, kErrPosition);
+        // Deposit.  Lanes with equal left node in a row (particles in
+        // lattice or sorted order share nodes) first add their weights in a
+        // segmented shuffle sum, and the segment's first lane does the two
+        // adds; a float64 add on shared memory is a compare-and-swap loop,
+        // which lanes hitting one node would otherwise serialise.
+        const int j = ok ? (int)fl : 0;
+        const int il = j < 0 ? j + ng : j, ir = j + 1 >= ng ? j + 1 - ng : j + 1;
+        const double f = s - fl;
+        const unsigned key = ok ? (unsigned)il : 0xffffffffu;
+        const unsigned kprev = __shfl_up_sync(kFull, key, 1);
+        const bool head = ok && (lane == 0 || kprev != key);
+        const unsigned heads = __ballot_sync(kFull, head || !ok);
+        const unsigned above = lane == 31 ? 0u : heads & (0xffffffffu << (lane + 1));
+        const int end = above ? __ffs(above) - 1 : 32;       // this lane's segment ends before
+        double sl = ok ? 1.0 - f : 0.0, sr = ok ? f : 0.0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double tl = __shfl_down_sync(kFull, sl, o);
+            const double tr = __shfl_down_sync(kFull, sr, o);
+            if (lane + o < end) {
+                sl += tl;
+                sr += tr;
+            }
         }
+        if (head) {
+            atomicAdd(&sRho[il], sl);
+            atomicAdd(&sRho[ir], sr);
+        }
+        if (valid && !ok) atomicOr(a.err, kErrPosition);
     }
     if (PUSH) {
         __syncthreads();
