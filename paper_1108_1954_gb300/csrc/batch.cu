@@ -85,37 +85,15 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
 
     // Block 0: the history rows of step s from the blocks' slice
-    // diagnostics.  Value f over the blocks: lane k of the value's 8 lanes
-    // reads block k, then a fixed butterfly over the lanes (f < kDiagFields:
-    // a slice diagnostic; kDiagFields, +1: the push sums; kDiagFields + 2:
-    // the integer charge); thread 0 writes the scalars and warp 1 the mode
-    // amplitudes.  Called for step s just before the next step's first
+    // diagnostics (cluster_diag_sums); thread 0 writes the scalars and warp 1
+    // the mode amplitudes.  Called for step s just before the next step's first
     // cluster barrier (where block 0 would wait for its peers anyway), or
     // after the last step: the peers rewrite their slice diagnostics only
     // after that barrier, and stay resident until block 0 has passed it.
     __shared__ double tot[kDiagFields + 2];
     __shared__ unsigned long long cqt;
     auto write_rows = [&](int s) {
-        static_assert(kMaxCluster == 8, "8 lanes per value");
-        constexpr int kSlots = (kDiagFields + 3) * 8;
-        for (int base = 0; base < kSlots; base += bs) {
-            const int u = base + tid, f = u >> 3, k = u & 7;
-            const bool isq = f == kDiagFields + 2;
-            const bool use = f < kDiagFields + 3 && k < C;
-            const int fd = f < kDiagFields + 2 ? f : 0;
-            const Exchange *pe = cl.map_shared_rank(&ex, k < C ? k : 0);
-            double sv = (use && !isq) ? (fd < kDiagFields ? pe->diag[fd] : pe->kv[fd - kDiagFields]) : 0.0;
-            unsigned long long sq = (use && isq) ? pe->cq : 0ull;
-#pragma unroll
-            for (int o = 1; o < 8; o <<= 1) {
-                sv += __shfl_xor_sync(kFull, sv, o);
-                sq += __shfl_xor_sync(kFull, sq, o);
-            }
-            if (f < kDiagFields + 3 && k == 0) {
-                if (isq) cqt = sq;
-                else tot[f] = sv;
-            }
-        }
+        cluster_diag_sums<kMaxCluster>(cl, ex, tot, &cqt);
         __syncthreads();                          // block 0 only
         const long long n = push ? step0 + s + 1 : step0 + s;
         pic_diag_row *row = &R.hist[n % R.hist_len];

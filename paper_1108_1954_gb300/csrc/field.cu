@@ -260,39 +260,7 @@ __device__ void cluster_finish(const SolveArgs &a, cg::cluster_group &cl, Cluste
     if (r == 0) {
         __shared__ double tot[kDiagFields + 2];
         __shared__ unsigned long long tot_cq;
-        // value f = u / 8 (f < kDiagFields + 2: a float64 field; f =
-        // kDiagFields + 2: the integer charge) from blocks 2k and 2k + 1,
-        // k = u mod 8, then a fixed butterfly over the value's 8 lanes: the
-        // remote reads are in flight together and the float64 sum is three
-        // levels deep.  u = t, t + T, ... (the trip count depends on the
-        // block size only, so every lane takes part in the shuffles).
-        static_assert(kMaxSolveCluster == 16, "8 lanes x 2 blocks per value");
-        constexpr int kSlots = (kDiagFields + 3) * 8;
-        for (int base = 0; base < kSlots; base += (int)blockDim.x) {
-            const int u = base + t, f = u >> 3, k = u & 7;
-            const bool isq = f == kDiagFields + 2;
-            const bool act = f < kDiagFields + 3;
-            const int fd = act && !isq ? f : 0;
-            double sv = 0.0;
-            unsigned long long sq = 0ull;
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int b = 2 * k + h;
-                const ClusterDiag *pe = cl.map_shared_rank(&cd, b < C ? b : 0);
-                const bool use = act && b < C;
-                sv += (use && !isq) ? (fd < kDiagFields ? pe->diag[fd] : pe->kv[fd - kDiagFields]) : 0.0;
-                sq += (use && isq) ? pe->cq : 0ull;
-            }
-#pragma unroll
-            for (int o = 1; o < 8; o <<= 1) {
-                sv += __shfl_xor_sync(kFull, sv, o);
-                sq += __shfl_xor_sync(kFull, sq, o);
-            }
-            if (act && k == 0) {
-                if (isq) tot_cq = sq;
-                else tot[f] = sv;
-            }
-        }
+        cluster_diag_sums<kMaxSolveCluster>(cl, cd, tot, &tot_cq);
         __syncthreads();
         const long long n = a.npartials > 0 ? step + 1 : step;
         pic_diag_row *row = &a.hist[n % a.hist_len];

@@ -2,6 +2,8 @@
 // the single-run solve (field.cu) and the batched cluster kernel (batch.cu).
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -225,6 +227,49 @@ __device__ __forceinline__ void node_diag(NodeDiag &d, int g, int ng, double E, 
         const float sn = sm * c1 + cm * s1;
         cm = cn;
         sm = sn;
+    }
+}
+
+// The cluster's diagnostics summed over its blocks, in one block (its
+// threads read the other blocks' shared memory).  T holds a block's slice
+// diagnostics: diag[kDiagFields], the push sums kv[2] and the integer charge
+// cq.  Value f (f < kDiagFields: diag[f]; kDiagFields, +1: kv; kDiagFields + 2:
+// cq) takes 8 lanes; lane k adds blocks KMAXC/8 k ... KMAXC/8 (k+1) - 1, then a
+// fixed xor butterfly over the 8 lanes.  All remote reads are in flight
+// together and the float64 sum is three levels deep.  The trip count depends
+// on the block size only, so every lane takes part in the shuffles (the block
+// size is a multiple of 32).
+template <int KMAXC, class T>
+__device__ __forceinline__ void cluster_diag_sums(cooperative_groups::cluster_group &cl, T &mine,
+                                                  double *tot, unsigned long long *tot_cq) {
+    static_assert(KMAXC == 8 || KMAXC == 16, "8 lanes per value");
+    constexpr int kPer = KMAXC / 8;
+    constexpr int kSlots = (kDiagFields + 3) * 8;
+    const int C = (int)cl.num_blocks(), t = threadIdx.x;
+    for (int base = 0; base < kSlots; base += (int)blockDim.x) {
+        const int u = base + t, f = u >> 3, k = u & 7;
+        const bool isq = f == kDiagFields + 2;
+        const bool act = f < kDiagFields + 3;
+        const int fd = act && !isq ? f : 0;
+        double sv = 0.0;
+        unsigned long long sq = 0ull;
+#pragma unroll
+        for (int h = 0; h < kPer; h++) {
+            const int b = kPer * k + h;
+            const T *pe = cl.map_shared_rank(&mine, b < C ? b : 0);
+            const bool use = act && b < C;
+            sv += (use && !isq) ? (fd < kDiagFields ? pe->diag[fd] : pe->kv[fd - kDiagFields]) : 0.0;
+            sq += (use && isq) ? pe->cq : 0ull;
+        }
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            sv += __shfl_xor_sync(kFull, sv, o);
+            sq += __shfl_xor_sync(kFull, sq, o);
+        }
+        if (act && k == 0) {
+            if (isq) *tot_cq = sq;
+            else tot[f] = sv;
+        }
     }
 }
 
