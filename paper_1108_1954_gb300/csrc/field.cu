@@ -310,8 +310,6 @@ struct SliceSums {
 
 __global__ void __launch_bounds__(kClusterSolveThreads) pic_solve_cluster_kernel(SolveArgs a) {
     cg::cluster_group cl = cg::this_cluster();
-    pdl_wait();                                  // the push's density and sums
-    pdl_trigger();
     __shared__ SliceSums ex;
     __shared__ ClusterDiag cd;
     __shared__ i128 sh[96];
@@ -427,8 +425,6 @@ __device__ __forceinline__ double warp_div(double num, double den) {
 
 __global__ void __launch_bounds__(kClusterSolveThreads) pic_solve_cg_kernel(SolveArgs a) {
     cg::cluster_group cl = cg::this_cluster();
-    pdl_wait();                                  // the push's density and sums
-    pdl_trigger();
     __shared__ double sv[kClusterSolveThreads + 2];   // v of the slice, ghost-padded
     __shared__ CgExchange ex;
     __shared__ ClusterDiag cd;
@@ -687,7 +683,7 @@ cudaError_t launch_solve(const SolveArgs &a, cudaStream_t s) {
         solve_cluster_shape(a.ng, a.solver == PIC_SOLVER_CG ? 32 : kSolveNodesPerBlock, &C,
                             &threads);
         cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute attr[2];
+        cudaLaunchAttribute attr[1];
         cfg.gridDim = dim3((unsigned)C, 1, 1);
         cfg.blockDim = dim3((unsigned)threads, 1, 1);
         cfg.dynamicSmemBytes = 0;
@@ -696,10 +692,8 @@ cudaError_t launch_solve(const SolveArgs &a, cudaStream_t s) {
         attr[0].val.clusterDim.x = (unsigned)C;
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
-        attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        attr[1].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = attr;
-        cfg.numAttrs = 2;
+        cfg.numAttrs = 1;
         if (a.solver == PIC_SOLVER_CG) return cudaLaunchKernelEx(&cfg, pic_solve_cg_kernel, a);
         return cudaLaunchKernelEx(&cfg, pic_solve_cluster_kernel, a);
     }

@@ -12,17 +12,6 @@ namespace pic {
 
 constexpr unsigned kFull = 0xffffffffu;   // all lanes of a warp
 
-// Programmatic dependent launch.  The push and the solve are launched with
-// programmatic stream serialization, so each may start while the kernel
-// before it on the stream is still running.  Each waits, before its first
-// read or write of global memory, until that kernel has completed and its
-// writes are visible (pdl_wait), and lets the kernel after it be scheduled as
-// soon as it starts (pdl_trigger): the next kernel's launch and block
-// scheduling overlap this one's tail instead of following it.  Without a
-// programmatic predecessor the wait returns at once.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
 // Fixed-point deposit: each particle adds exactly 2^24 to the density sum.
 constexpr int kFixBits = 24;
 constexpr uint32_t kFixOne = 1u << kFixBits;

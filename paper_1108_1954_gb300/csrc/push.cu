@@ -92,8 +92,6 @@ template <int VARIANT, bool PUSH, int U>
 __global__ void __launch_bounds__(512) pic_push_fixed_kernel(PushArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double red[64];
-    pdl_wait();                                  // E, x, v and rho_q of the kernel before
-    pdl_trigger();
     constexpr bool kPacked = VARIANT == PIC_DEPOSIT_PACKED || VARIANT == kMatchPacked;
     const PushConsts c = a.c;
     const int ng = c.ng;
@@ -623,22 +621,8 @@ cudaError_t launch_push_fixed(const PushArgs &a, int grid, int block, int varian
                               int unroll, bool push, cudaStream_t s) {
     FixedKernel k = pick_fixed(variant, push, unroll);
     if (!k) return cudaErrorInvalidValue;
-    if (variant == PIC_DEPOSIT_QUAD_BULK && push) {
-        k<<<grid, block, fixed_smem_bytes(variant, push, a.c.ng), s>>>(a);
-        return cudaGetLastError();
-    }
-    // the per-thread kernels wait for their predecessor on the device
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    cfg.gridDim = dim3((unsigned)grid, 1, 1);
-    cfg.blockDim = dim3((unsigned)block, 1, 1);
-    cfg.dynamicSmemBytes = fixed_smem_bytes(variant, push, a.c.ng);
-    cfg.stream = s;
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k, a);
+    k<<<grid, block, fixed_smem_bytes(variant, push, a.c.ng), s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_push_f32_atomic(const PushArgsF32Atomic &a, int grid, int block,
