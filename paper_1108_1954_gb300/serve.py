@@ -46,6 +46,7 @@ class Record:
     npart: int = 0
     steps: int = 0
     result: object = None     # last diagnostics row, or (state, field) if kept
+    rejected: bool = False    # larger than the whole pool: never admitted
 
     @property
     def latency(self) -> float:
@@ -110,6 +111,11 @@ class Server:
                 records[req.rid] = Record(req.rid, req.arrival, admitted=now(),
                                           npart=req.params.npart, steps=req.steps)
             if not inflight:
+                # what an empty pool cannot admit never fits: reject it
+                while waiting:
+                    req = waiting.popleft()
+                    records[req.rid] = Record(req.rid, req.arrival, npart=req.params.npart,
+                                              steps=req.steps, rejected=True)
                 if pending:
                     time.sleep(max(0.0, min(pending[0].arrival - now(), 0.005)))
                 continue
@@ -128,9 +134,11 @@ class Server:
                 pool.release(slot)
         wall = now()
         recs = [records[r.rid] for r in sorted(requests, key=lambda r: r.rid)]
-        lat = np.array([r.latency for r in recs])
-        work = float(sum(r.npart * r.steps for r in recs))
-        stats = dict(requests=len(recs), wall_s=wall, advances=advances,
+        done = [r for r in recs if not r.rejected]
+        lat = np.array([r.latency for r in done]) if done else np.zeros(1)
+        work = float(sum(r.npart * r.steps for r in done))
+        stats = dict(requests=len(recs), rejected=len(recs) - len(done), wall_s=wall,
+                     advances=advances,
                      advance_steps=self.k, mean_active=active_sum / max(1, advances),
                      p50_s=float(np.percentile(lat, 50)), p99_s=float(np.percentile(lat, 99)),
                      mean_s=float(lat.mean()), particle_steps=work,

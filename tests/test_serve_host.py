@@ -1,0 +1,140 @@
+"""The serving loop's host logic on the CPU, against a stand-in pool.
+
+`serve.Server.serve` only sequences pool calls (admit, advance, finished,
+diagnostics, release).  A stand-in pool with a byte budget and step counters
+checks, without a GPU: every request finishes with its own step count; a head
+request that does not fit does not block smaller ones behind it; requests that
+arrive while others are resident join the same advances (continuous
+batching); kept requests return their state, field and history.
+"""
+import time
+
+import numpy as np
+
+from paper_1108_1954_gb300 import Loading, Params, serve
+
+
+class FakePool:
+    def __init__(self, budget, max_slots=8, history=8):
+        self.budget, self.max_slots, self.history = budget, max_slots, history
+        self.used = 0
+        self.runs = {}          # slot -> [params, steps, done, bytes]
+        self.next_slot = 0
+        self.log = []           # (event, slot, resident count)
+
+    @staticmethod
+    def bytes_of(p):
+        return 16 * p.npart + 64 * p.ncell
+
+    def admit_loaded(self, params, loading, steps):
+        b = self.bytes_of(params)
+        if len(self.runs) >= self.max_slots or self.used + b > self.budget:
+            return None
+        slot = self.next_slot
+        self.next_slot += 1
+        self.runs[slot] = [params, steps, 0, b]
+        self.used += b
+        self.log.append(("admit", slot, len(self.runs)))
+        return slot
+
+    def advance(self, k):
+        time.sleep(0.0005)      # an advance takes time, as on the device
+        active = 0
+        for r in self.runs.values():
+            if r[2] < r[1]:
+                r[2] = min(r[1], r[2] + k)
+                active += 1
+        self.log.append(("advance", -1, active))
+        return active
+
+    def finished(self):
+        return [s for s, r in self.runs.items() if r[2] >= r[1]]
+
+    def diagnostics(self, slot, first, count):
+        rows = np.zeros(count, dtype=[("step", "i8"), ("field", "f8")])
+        rows["step"] = np.arange(first, first + count)
+        return rows
+
+    def get_state(self, slot):
+        n = self.runs[slot][0].npart
+        return np.zeros(n, np.float32), np.zeros(n, np.float32)
+
+    def get_field(self, slot):
+        return dict(E=np.zeros(self.runs[slot][0].ncell))
+
+    def release(self, slot):
+        r = self.runs.pop(slot)
+        self.used -= r[3]
+        self.log.append(("release", slot, len(self.runs)))
+
+
+def make_server(pool, k):
+    srv = serve.Server.__new__(serve.Server)    # no device pool
+    srv.pool, srv.k, srv.history = pool, k, pool.history
+    return srv
+
+
+def request(rid, arrival, npart, ncell, steps):
+    return serve.Request(rid, arrival, Params(npart=npart, ncell=ncell, length=1.0),
+                         Loading(v0=0.1, vth=0.0, seed=rid), steps)
+
+
+def test_every_request_finishes_with_its_steps():
+    pool = FakePool(budget=10 ** 9)
+    reqs = [request(i, 0.002 * i, 1000 + 10 * i, 64, 30 + 7 * i) for i in range(12)]
+    recs, stats = make_server(pool, 10).serve(reqs)
+    assert [r.rid for r in recs] == list(range(12))
+    for r, q in zip(recs, reqs):
+        assert r.steps == q.steps and r.npart == q.params.npart
+        assert r.finished >= r.admitted >= r.arrival - 1e-9
+        assert int(r.result["step"]) == q.steps              # the last history row
+    assert stats["requests"] == 12 and stats["particle_steps"] == sum(
+        q.params.npart * q.steps for q in reqs)
+    assert not pool.runs and pool.used == 0                   # everything released
+
+
+def test_a_head_that_does_not_fit_does_not_block():
+    resident = request(0, 0.0, 900, 64, 200)
+    big = request(1, 0.0, 1000, 64, 20)
+    small = request(2, 0.0, 100, 64, 20)
+    # the budget holds `resident` + `small`, or `big` alone, not `resident` + `big`
+    budget = FakePool.bytes_of(resident.params) + FakePool.bytes_of(small.params) + 1
+    assert FakePool.bytes_of(big.params) <= budget
+    pool = FakePool(budget=budget)
+    recs, stats = make_server(pool, 10).serve([resident, big, small])
+    admitted = [s for e, s, _ in pool.log if e == "admit"]
+    # slots in admission order: resident (0), small (1) while big waits, big (2)
+    assert admitted == [0, 1, 2]
+    assert recs[2].admitted < recs[1].admitted               # small passed big
+    assert recs[1].admitted >= recs[0].finished - 1e-9       # big after resident left
+    assert stats["rejected"] == 0
+
+
+def test_a_request_larger_than_the_pool_is_rejected():
+    pool = FakePool(budget=10 ** 5)
+    reqs = [request(0, 0.0, 10 ** 6, 64, 20), request(1, 0.001, 100, 64, 20)]
+    recs, stats = make_server(pool, 10).serve(reqs)
+    assert recs[0].rejected and recs[0].result is None
+    assert not recs[1].rejected and int(recs[1].result["step"]) == 20
+    assert stats["rejected"] == 1 and stats["particle_steps"] == 100 * 20
+
+
+def test_late_arrivals_join_running_advances():
+    pool = FakePool(budget=10 ** 9)
+    reqs = [request(0, 0.0, 1000, 64, 400)] + [
+        request(i, 0.01 + 0.002 * i, 500, 64, 40) for i in range(1, 6)]
+    recs, stats = make_server(pool, 5).serve(reqs)
+    # some advance moved the first run together with later ones
+    assert max(a for e, _, a in pool.log if e == "advance") >= 2
+    assert all(r.finished < recs[0].finished for r in recs[1:])
+    assert stats["mean_active"] > 1.0
+
+
+def test_kept_requests_return_state_field_and_history():
+    pool = FakePool(budget=10 ** 9, history=64)
+    reqs = [request(0, 0.0, 300, 32, 20), request(1, 0.0, 300, 32, 20)]
+    recs, _ = make_server(pool, 7).serve(reqs, keep={1})
+    (x, v), field, hist = recs[1].result
+    assert x.shape == (300,) and field["E"].shape == (32,)
+    assert hist["step"].tolist() == list(range(21))
+    assert int(recs[0].result["step"]) == 20
