@@ -8,6 +8,7 @@
 //   x[N], v[N] (float32), E32[NG], E64[NG], phi[NG], rho[NG], rho_q_last[NG],
 //   history[H], step counter.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -416,7 +417,9 @@ int pic_pool_advance(pic_pool *pool, int64_t k, int32_t *active) {
         pic_pool::Slot &sl = pool->slots[i];
         if (!sl.used) continue;
         const int64_t left = sl.target - sl.done;
-        sl.desc.steps = (int)(left < k ? left : k);
+        const int64_t take = left < k ? left : k;
+        // one launch advances at most INT_MAX steps (the descriptor's int)
+        sl.desc.steps = (int)(take > INT_MAX ? INT_MAX : take);
         if (sl.desc.steps > 0) order.push_back(i);
     }
     // longest work first (particles x steps)
