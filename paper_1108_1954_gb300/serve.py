@@ -25,7 +25,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import Loading, Params, Pool, pool_run_bytes
+from . import PIC_EINVAL, Loading, Params, PicError, Pool, pool_run_bytes
 
 
 @dataclass
@@ -46,7 +46,7 @@ class Record:
     npart: int = 0
     steps: int = 0
     result: object = None     # last diagnostics row, or (state, field) if kept
-    rejected: bool = False    # larger than the whole pool: never admitted
+    rejected: bool = False    # invalid for the pool, or larger than all of it
 
     @property
     def latency(self) -> float:
@@ -103,7 +103,17 @@ class Server:
             # admit what fits, oldest first; a head that does not fit does not
             # block smaller requests behind it
             for req in list(waiting):
-                slot = pool.admit_loaded(req.params, req.loading, req.steps)
+                try:
+                    slot = pool.admit_loaded(req.params, req.loading, req.steps)
+                except PicError as e:
+                    if e.code != PIC_EINVAL:
+                        raise
+                    # a request the pool cannot run (e.g. more cells than it
+                    # was built for) is rejected, not served
+                    waiting.remove(req)
+                    records[req.rid] = Record(req.rid, req.arrival, npart=req.params.npart,
+                                              steps=req.steps, rejected=True)
+                    continue
                 if slot is None:
                     continue
                 waiting.remove(req)

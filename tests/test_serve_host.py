@@ -11,7 +11,7 @@ import time
 
 import numpy as np
 
-from paper_1108_1954_gb300 import Loading, Params, serve
+from paper_1108_1954_gb300 import PIC_EINVAL, Loading, Params, PicError, serve
 
 
 class FakePool:
@@ -27,6 +27,8 @@ class FakePool:
         return 16 * p.npart + 64 * p.ncell
 
     def admit_loaded(self, params, loading, steps):
+        if params.ncell > 4096:                 # beyond the pool's grid limit
+            raise PicError(PIC_EINVAL, "pic_pool_admit_loaded")
         b = self.bytes_of(params)
         if len(self.runs) >= self.max_slots or self.used + b > self.budget:
             return None
@@ -117,6 +119,14 @@ def test_a_request_larger_than_the_pool_is_rejected():
     assert recs[0].rejected and recs[0].result is None
     assert not recs[1].rejected and int(recs[1].result["step"]) == 20
     assert stats["rejected"] == 1 and stats["particle_steps"] == 100 * 20
+
+
+def test_an_invalid_request_is_rejected_not_fatal():
+    pool = FakePool(budget=10 ** 9)
+    reqs = [request(0, 0.0, 100, 8192, 20), request(1, 0.0, 100, 64, 20)]
+    recs, stats = make_server(pool, 10).serve(reqs)
+    assert recs[0].rejected and not recs[1].rejected
+    assert stats["rejected"] == 1
 
 
 def test_late_arrivals_join_running_advances():
