@@ -70,6 +70,9 @@ class Server:
     def __init__(self, arena_bytes: int, max_slots: int = 1024, ncell_max: int = 4096,
                  history: int = 8, advance_steps: int = 50, variant: int = 5,
                  cluster: int = 8, block: int = 512, device=None):
+        if int(advance_steps) < 1:
+            # advance(0) only initialises: no run would ever finish
+            raise ValueError("advance_steps must be at least 1")
         self.pool = Pool(max_slots=max_slots, ncell_max=ncell_max, arena_bytes=arena_bytes,
                          history=history, variant=variant, cluster=cluster, block=block,
                          device=device)

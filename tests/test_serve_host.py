@@ -10,6 +10,7 @@ batching); kept requests return their state, field and history.
 import time
 
 import numpy as np
+import pytest
 
 from paper_1108_1954_gb300 import PIC_EINVAL, Loading, Params, PicError, serve
 
@@ -148,3 +149,9 @@ def test_kept_requests_return_state_field_and_history():
     assert x.shape == (300,) and field["E"].shape == (32,)
     assert hist["step"].tolist() == list(range(21))
     assert int(recs[0].result["step"]) == 20
+
+
+def test_a_server_that_never_advances_is_refused():
+    # checked before any device pool is made
+    with pytest.raises(ValueError):
+        serve.Server(arena_bytes=1 << 20, advance_steps=0)
