@@ -346,7 +346,8 @@ typedef struct pic_pool_config {
 } pic_pool_config;
 
 /* Arena bytes one run with parameters *p takes in a pool with `history`
- * rows (float32 particles, PIC_FP32_FIXED only). */
+ * rows.  PIC_EINVAL for what no pool admits: a precision other than
+ * PIC_FP32_FIXED, the CG solver, the NGP shape, history < 1. */
 int pic_pool_run_bytes(const pic_params *p, int32_t history, size_t *bytes);
 
 /* Bytes at the start of the arena for the pool's own tables. */

@@ -220,6 +220,7 @@ int pic_pool_run_bytes(const pic_params *p, int32_t history, size_t *bytes) {
     int rc = validate_params(p);
     if (rc) return rc;
     if (p->precision != PIC_FP32_FIXED) return PIC_EINVAL;
+    if (p->field_solver != PIC_SOLVER_EXACT || p->shape != PIC_SHAPE_CIC) return PIC_EINVAL;
     *bytes = run_layout(p, history).total;
     return PIC_OK;
 }

@@ -76,3 +76,51 @@ def test_calls_on_null_run_are_rejected(pic):
     assert lib.pic_step_n(None, 1) == pic.PIC_EINVAL
     assert lib.pic_solve_field(None) == pic.PIC_EINVAL
     assert lib.pic_step_count(None) == -1
+
+
+@pytest.mark.parametrize("bad", [
+    dict(qm=float("inf")), dict(dt=float("inf")), dict(rho_ion=-1.0), dict(history=-1),
+    dict(blocks_per_sm=-1), dict(blocks_per_sm=33), dict(unroll=8), dict(field_solver=2),
+    dict(cg_iterations=-1), dict(cg_iterations=100001), dict(shape=2),
+    dict(shape=1, precision=2), dict(shape=1, precision=1)])
+def test_more_invalid_parameters_rejected(pic, bad):
+    with pytest.raises(pic.PicError) as e:
+        pic.workspace_size(_params(pic, **bad))
+    assert e.value.code == pic.PIC_EINVAL
+
+
+def test_reserved_word_must_be_zero(pic):
+    p = _params(pic).c()
+    n = C.c_size_t(0)
+    assert pic._lib.pic_workspace_size(C.byref(p), C.byref(n)) == pic.PIC_OK
+    p.reserved = 1
+    assert pic._lib.pic_workspace_size(C.byref(p), C.byref(n)) == pic.PIC_EINVAL
+
+
+def test_pool_run_bytes(pic):
+    a = pic.pool_run_bytes(_params(pic, npart=1 << 20), 8)
+    b = pic.pool_run_bytes(_params(pic, npart=1 << 21), 8)
+    # x and v in float32: 8 B per particle, plus alignment
+    assert 8 * (1 << 20) <= b - a <= 8 * (1 << 20) + 4096
+    c = pic.pool_run_bytes(_params(pic, npart=1 << 20), 1000)
+    assert c > a                                       # history rows
+    for bad, h in [(dict(precision=pic.PIC_FP64), 8), (dict(precision=pic.PIC_FP32_ATOMIC), 8),
+                   (dict(field_solver=1), 8), (dict(shape=1), 8), ({}, 0), (dict(npart=0), 8)]:
+        with pytest.raises(pic.PicError) as e:
+            pic.pool_run_bytes(_params(pic, **bad), h)
+        assert e.value.code == pic.PIC_EINVAL
+
+
+def test_pool_table_bytes(pic):
+    def table(*cfg):
+        c = pic.CPoolConfig(*cfg)
+        n = C.c_size_t(0)
+        rc = pic._lib.pic_pool_table_bytes(C.byref(c), C.byref(n))
+        return rc, n.value
+    rc1, t1 = table(16, 4096, 8, 0, 0, 0)
+    rc2, t2 = table(1024, 4096, 8, 0, 0, 0)
+    assert rc1 == rc2 == pic.PIC_OK and t2 > t1 > 0
+    for bad in [(0, 4096, 8, 0, 0, 0), (16, 0, 8, 0, 0, 0), (16, 8193, 8, 0, 0, 0),
+                (16, 4096, 0, 0, 0, 0)]:
+        assert table(*bad)[0] == pic.PIC_EINVAL
+    assert pic._lib.pic_pool_table_bytes(None, None) == pic.PIC_EINVAL
