@@ -55,8 +55,19 @@ def fp32_field_bound(n, ng, L):
     of Eq. 6 only sees the ~N/NG particles between nodes g and g+1:
     |dS_g| ~ (NG/N) sqrt(N/NG) NG 2^-24.  E_g = (L/(2 NG)) (S_g + S_{g-1} -
     2 mean S) then gives |dE| ~ L sqrt(NG/N) 2^-24; 16 times that covers the
-    largest of 8192 nodes with room."""
-    return 16.0 * L * math.sqrt(ng / n) * 2.0 ** -24 + 1e-15
+    largest of 8192 nodes with room.
+
+    A second term does not shrink with N.  The scale c itself is float32,
+    c = (float)(NG/L) = (NG/L)(1 + eta) with |eta| <= 2^-24, so the fixed-point
+    recipe sees every particle at x (1 + eta): the plasma stretched about
+    x = 0.  A sliver of the electrons' charge, |eta| L rho_ion, crosses the
+    periodic boundary (or leaves a gap before it), a point charge at the wrap
+    on a uniform background, whose field is a sawtooth of amplitude
+    |eta| L rho_ion / 2.  At NG = 4096 on L = 4 pi that is 2.53e-7, larger than
+    the first term from N ~ 2^22 on."""
+    c = ng / L
+    eta = float(np.float32(c)) / c - 1.0
+    return 16.0 * L * math.sqrt(ng / n) * 2.0 ** -24 + 0.5 * abs(eta) * L + 1e-15
 
 
 def one_step_parity(n, ng, L, seed, v0=0.2, vth=0.01, **kw):
