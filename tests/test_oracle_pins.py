@@ -345,3 +345,35 @@ def test_fixed_deposit_exact_total_and_fp64_agreement():
     # most a few units of 2^-24 * NG, so rho differs by <~ (NG/N) * count * that
     assert np.abs(rho_fix - rho64).max() < 1e-5
     assert abs(rho_fix.sum()) < 1e-10
+
+
+def _lattice_fields(n, ng, lx):
+    x, v = W.lattice_positions(n, lx), np.zeros(n)
+    x32, _ = W.to_f32_state(x, v, lx)
+    p = O.params(ng, n, lx)
+    E_fix = O.field(p, O.rho_from_fixed(p, O.deposit_fixed(ng, lx, x32)))[1]
+    E_64 = O.field(p, O.deposit(p, x32.astype(np.float64)))[1]
+    return E_fix, E_64
+
+
+def test_fixed_deposit_float32_scale_ramp():
+    # The recipe's scale c = (float)(NG/L) = (NG/L)(1 + eta) places every
+    # particle at x (1 + eta): the plasma stretched by 1 + eta, a charge
+    # |eta| L rho_ion carried across the wrap.  On a uniform lattice, whose
+    # FP64 field is zero, the fixed-point field is the ramp that charge
+    # makes: dE/dx = eta rho_ion between the wrap's two ends (E rises by
+    # eta L over the box), amplitude |eta| L / 2.
+    n, ng, lx = 1 << 22, 1024, L4PI
+    c = ng / lx
+    eta = float(np.float32(c)) / c - 1.0
+    amp = 0.5 * abs(eta) * lx
+    assert amp > 2e-7
+    E_fix, E_64 = _lattice_fields(n, ng, lx)
+    assert np.abs(E_64).max() < 0.02 * amp
+    g = np.arange(1, ng - 1)
+    slope = np.polyfit(g, E_fix[1:-1], 1)[0]
+    assert abs(slope * ng / (eta * lx) - 1.0) < 0.05
+    assert abs(np.abs(E_fix).max() / amp - 1.0) < 0.1
+    # a box whose scale is exact in float32 (c = 10) has no ramp
+    E_fix, _ = _lattice_fields(1 << 20, 100, 10.0)
+    assert np.abs(E_fix).max() < 1e-3 * 0.5 * 2.0 ** -24 * 10.0
