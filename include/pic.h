@@ -92,8 +92,8 @@ extern "C" {
  * field comes back (Sec. 2.3 and Sec. 2), nodes at the cell centres.
  *   CIC  the two-cell linear weighting of Sec. 2.3 and the listing (default);
  *   NGP  nearest grid point: the cell the particle belongs to, floor(x NG/L)
- *        in float32, takes its whole charge and gives its field (Sec. 2's
- *        "counting the particles of a cell").  PIC_FP32_FIXED only; single
+ *        in float32, takes its whole charge and gives its field (Sec. 2: a
+ *        cell's density is the count of its particles).  PIC_FP32_FIXED only; single
  *        runs only (the pool rejects it). */
 #define PIC_SHAPE_CIC 0
 #define PIC_SHAPE_NGP 1
@@ -166,8 +166,8 @@ int pic_create(const pic_params *p, void *workspace, size_t workspace_bytes,
 /* Release the host handle and its CUDA graphs (not the workspace). */
 void pic_destroy(pic_run *run);
 
-/* Load the initial state and make E^0 ready (Sec. 2 "initialization"; the
- * Appendix A set-up).  x0, v0: host arrays of N values in the run's precision
+/* Load the initial state and make E^0 ready (Sec. 2, the initial set-up;
+ * Appendix A).  x0, v0: host arrays of N values in the run's precision
  * (float for the FP32 modes, double for PIC_FP64); v0 is v^{-1/2}.  Positions
  * must lie in [0, L).  Copies them to the device, deposits rho^0, solves Phi^0
  * and E^0 and resets the step counter to 0.  Synchronises the stream (the host
@@ -269,8 +269,8 @@ int pic_device_arrays(pic_run *run, void **x, void **v, void **E32);
 int pic_launch_shape(const pic_run *run, int32_t *grid, int32_t *block,
                      int32_t *variant, int32_t *unroll);
 
-/* Device-side initial loading of a two-stream plasma (Sec. 2 "initialization",
- * the Appendix A set-up, the Sec. 4 beams).  Particle j of N:
+/* Device-side initial loading of a two-stream plasma (Sec. 2, the initial set-up;
+ * Appendix A; the Sec. 4 beams).  Particle j of N:
  *   x = (j + 1/2) L/N - sum_m (eps_m/k_m) sin(k_m x0 + phase_m), k_m = 2 pi m/L,
  *       folded into [0, L), float32 (a value rounding to L is 0);
  *   v = s_j v0 + vth sqrt(-2 ln u1) cos(2 pi u2), s_j = +1 (j even) / -1 (odd),
