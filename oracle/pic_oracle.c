@@ -221,7 +221,7 @@ int orc_field_cg(const orc_params *p, const double *rho, int maxit,
 }
 
 /* Electric field by central difference (Sec. 2.2, Eq. 7) with periodic
- * neighbours at both ends (Appendix A "calculate the electric field"). */
+ * neighbours at both ends (Appendix A, the electric-field step). */
 void orc_efield(const orc_params *p, const double *phi, double *E)
 {
     const int ng = p->ng;
@@ -233,8 +233,8 @@ void orc_efield(const orc_params *p, const double *phi, double *E)
     }
 }
 
-/* Field at the particles, grid to particle (Sec. 2.3 "the same mechanism";
- * Appendix A velocity loop): Ex = w2 E[ig] + w1 E[ig-1] with the same
+/* Field at the particles, grid to particle (Sec. 2.3: the deposit's weighting
+ * used in reverse; Appendix A velocity loop): Ex = w2 E[ig] + w1 E[ig-1] with the same
  * weights and periodic ends as orc_deposit. */
 int orc_gather(const orc_params *p, const double *xp, const double *E,
                double *Ex)
