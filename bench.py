@@ -17,8 +17,8 @@ CUDA-event duration against the measured copy bandwidth; `cpu_baseline` is the
 FP64 oracle on this host.
 
 `--impl reference` times the FP64 oracle (the reference arm) on the same
-workload: each step is the oracle's step over a bounded sample of 2^20
-particles of the same state.
+workload: each step is the oracle's step over a bounded sample, the same
+recipe (cells, box, beams, modes, seed) at 2^20 electrons.
 Under torchrun each rank runs its own independent run (weak scaling, no
 collective on the data path).
 """
@@ -725,10 +725,14 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        x32, v32 = make_state(w)
+        # a bounded sample of the workload: the same recipe (cells, box,
+        # beams, modes, seed) at REF_SAMPLE electrons, so that its density
+        # and field are those of the full run
+        ws_ = dict(w, npart=min(REF_SAMPLE, w["npart"]))
+        x32, v32 = make_state(ws_)
         K, Wm = args.steps, args.warmup
-        time_oracle(w, x32, v32, sample=REF_SAMPLE, steps=max(1, Wm))
-        r = time_oracle(w, x32, v32, sample=REF_SAMPLE, steps=max(1, K))
+        time_oracle(ws_, x32, v32, steps=max(1, Wm))
+        r = time_oracle(ws_, x32, v32, steps=max(1, K))
         line = {
             "impl": "reference", "metric": "particle-steps/s",
             "value": r["value"], "unit": "particle-steps/s", "n_gpus": args.gpus,
@@ -739,7 +743,8 @@ def main():
                        % (w["npart"], w["ncell"], r["npart"])},
             "cpu_baseline": {"value": r["value"], "unit": "particle-steps/s", "cores": 1,
                              "kind": "oracle",
-                             "sample": "FP64 oracle, first %d particles of the state, %d steps"
+                             "sample": "FP64 oracle, the same recipe at %d electrons "
+                                       "(cells, box, beams, modes unchanged), %d steps"
                              % (r["npart"], r["steps"])},
             "e2e": {"value": r["value"], "unit": "particle-steps/s",
                     "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
