@@ -84,8 +84,8 @@ def parse():
                          "at several points of the config-2 run")
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-advance", type=int, default=50)
-    ap.add_argument("--precision", action="store_true",
-                    help="add the precision study (config 4)")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="leave out the precision study (config 4)")
     ap.add_argument("--precision-steps", type=int, default=2000)
     ap.add_argument("--precision-oracle-steps", type=int, default=150)
     return ap.parse_args()
@@ -511,10 +511,8 @@ def variant_scan(args):
         xs, vs = run.get_state()
         st = run.step
         row = {"step": st}
-        for var in (1, 2, 5, 6, 7):
+        for var in (1, 2, 5, 6):
             for blk, un in ((512, 1), (512, 2), (256, 1)):
-                if var == 7 and (blk, un) != (512, 1):
-                    continue          # the bulk-copy kernel has one shape
                 run.set_state(xs, vs, st)
                 run.set_launch(var, blk, un)
                 ev = [(torch.cuda.Event(True), torch.cuda.Event(True)) for _ in range(2 * S)]
@@ -717,6 +715,53 @@ def time_oracle(w, x32, v32, budget_s=12.0, sample=None, steps=None):
     return dict(value=n * done / el, steps=done, npart=n, seconds=el)
 
 
+def sig(x, digits=4):
+    """x rounded to `digits` significant digits (floats only)."""
+    if isinstance(x, float) and math.isfinite(x) and x != 0.0:
+        return float("%.*g" % (digits, x))
+    return x
+
+
+def compact_weak(w):
+    """The weak-scaling section as parallel lists (time per cycle in us and
+    the paper's speed-up measure), short enough for a log tail."""
+    out = {"P": w["cores"], "steps": w["steps"]}
+    for name in ("cg150", "exact"):
+        out[name + "_us_per_step"] = [sig(r["us_per_step"], 4) for r in w[name]]
+        out[name + "_speedup"] = [sig(r["speedup"], 4) for r in w[name]]
+    out["paper_speedup"] = [w["paper_speedup"][P] for P in w["cores"]]
+    out["stacked_particle_steps_per_s"] = sig(w["stacked"]["particle_steps_per_s"])
+    return out
+
+
+def compact_precision(pr):
+    """Config 4, one row per precision mode against the FP64 oracle."""
+    out = {"npart": pr["npart"], "ncell": pr["ncell"], "steps": pr["steps"],
+           "oracle_steps": pr["oracle"]["steps"], "oracle_gamma1": sig(pr["oracle"]["gamma1"]),
+           "gamma_theory": sig(pr["gamma_theory"])}
+    for name in ("fp64", "fp32_atomic", "fp32_fixed"):
+        r = pr[name]
+        out[name] = {"particle_steps_per_s": sig(r["particle_steps_per_s"], 3),
+                     "energy_drift": sig(r["energy_drift"], 3),
+                     "momentum_error": sig(r["momentum_error"], 2),
+                     "gamma1_vs_oracle": sig(r["gamma1_vs_oracle"], 2),
+                     "field_energy_vs_oracle": sig(r["field_energy_vs_oracle"], 2)}
+    return out
+
+
+def compact_batched(b):
+    return {"runs": b["runs"], "steps": b["steps"], "particles": b["particles"],
+            "value": sig(b["value"]), "plain_value": sig(b["plain_value"]),
+            "speedup_vs_plain": sig(b["speedup_vs_plain"], 3), "unit": b["unit"],
+            "launch": b["launch"], "tune_top": b["tune"][:3]}
+
+
+def compact_served(sv):
+    keys = ("requests", "rejected", "p50_s", "p99_s", "mean_s", "value", "unit", "wall_s",
+            "arrival_rate_per_s", "advance_steps", "mean_active")
+    return {k: sig(sv[k]) for k in keys if k in sv}
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -778,7 +823,7 @@ def main():
     batched = None if args.no_batched else time_batched(args)
     served = None if args.no_served else time_served(args)
     weak = None if args.no_weak else time_weak(args)
-    precision = precision_study(args) if (args.precision and rank == 0) else None
+    precision = precision_study(args) if (not args.no_precision and rank == 0) else None
 
     n, K = w["npart"], res["steps"]
     value, total_s = rank_aggregate(res["total_ms"] / 1e3, n, K, ws, device="cuda")
@@ -838,16 +883,19 @@ def main():
                        "d2h_bytes_per_step": e2e["d2h_per_step"]}
     if cpu is not None:
         line["cpu_baseline"] = cpu
-    if c1 is not None:
-        line["c1"] = c1
-    if batched is not None:
-        line["batched"] = batched
-    if served is not None:
-        line["served"] = served
+    # the sections of the metric beyond the single run come last, compact,
+    # so that the end of the line carries them: weak scaling, config 1, the
+    # precision study, batched vs plain, served latency
     if weak is not None:
-        line["weak"] = weak
+        line["weak"] = compact_weak(weak)
+    if c1 is not None:
+        line["c1"] = {k: sig(v) for k, v in c1.items()}
     if precision is not None:
-        line["precision"] = precision
+        line["precision"] = compact_precision(precision)
+    if batched is not None:
+        line["batched"] = compact_batched(batched)
+    if served is not None:
+        line["served"] = compact_served(served)
     print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -56,7 +56,9 @@ extern "C" {
 #define PIC_EINVAL (-1)   /* bad argument or parameter                       */
 #define PIC_ENOMEM (-2)   /* workspace too small / pool budget exhausted      */
 #define PIC_ECUDA (-3)    /* a CUDA runtime call failed                       */
-#define PIC_ETIMEOUT (-4) /* a bounded device wait ran out                     */
+#define PIC_ETIMEOUT (-4) /* reserved: no call waits on the device with a
+                             time limit (every device wait is a hardware
+                             block or cluster barrier)                      */
 #define PIC_EDEVICE (-5)  /* a kernel flagged bad particle data                */
 #define PIC_ESTATE (-6)   /* call out of order (e.g. push before init)         */
 
@@ -65,21 +67,16 @@ extern "C" {
 #define PIC_FP32_ATOMIC 1 /* float32 push, float32 atomic deposit              */
 #define PIC_FP64 2        /* float64 push, float64 atomic deposit              */
 
-/* Deposit-kernel variants of the fused push (PIC_FP32_FIXED only). */
+/* Deposit-kernel variants of the fused push (PIC_FP32_FIXED only); all give
+ * the same integers.  The values 3, 4 and 7 are not variants (PIC_EINVAL). */
 #define PIC_DEPOSIT_AUTO 0   /* chosen by the library                        */
 #define PIC_DEPOSIT_ATOMIC 1 /* two shared-memory atomics per particle       */
 #define PIC_DEPOSIT_MATCH 2  /* warp groups of equal cell (match + reduce)   */
-#define PIC_DEPOSIT_PACKED 3 /* count and weight packed in one atomic        */
-#define PIC_DEPOSIT_MATCH_PACKED 4 /* warp groups, one packed atomic each   */
 #define PIC_DEPOSIT_QUAD 5         /* runs within a thread's 4 particles,
                                       two atomics per run                  */
 #define PIC_DEPOSIT_PAIR 6         /* QUAD with two open runs per thread, so
                                       particles of two interleaved cells (two
                                       beams before a sort) still combine    */
-#define PIC_DEPOSIT_QUAD_BULK 7    /* QUAD, with the particle tiles moved
-                                      between HBM and shared memory by bulk
-                                      copies (cp.async.bulk, mbarrier); 512
-                                      threads, unroll 1                     */
 
 /* Field solvers (pic_params.field_solver).  Both solve the Eq. 6 system with
  * Phi_0 = 0 (the gauge the paper pins).
@@ -214,15 +211,24 @@ int pic_sync(pic_run *run);
  * PIC_SORT_NOALLOC_SCRATCH bytes inside the library, which every GPU that
  * loads the library keeps until the process exits.
  * x, v: n float32 positions and velocities (device memory); x_out, v_out:
- * n float32 each (device memory, not the inputs), receiving the particles
- * ordered by cell trunc(x NG/L) (clamped to [0, NG-1]), particles of one cell
- * in their input order.  Limits: 1 <= n <= 2^32 - 1, 1 <= ncell <=
- * PIC_NCELL_MAX, else PIC_EINVAL; larger n only uses fewer, longer chunks to
- * keep the tables inside the array.  Enqueued on `stream`, asynchronous.  The
- * first call on a device looks up the array's device address with that device
- * current: make it before any stream capture.  Every call shares the array and
- * leaves its contents behind (each call rewrites its tables in full and clears
- * the error word first); calls whose work overlaps on the GPU race on it. */
+ * n float32 each (device memory), receiving the particles ordered by cell
+ * trunc(x c), c = (float)(NG/L), clamped to [0, NG-1] (NaN to cell 0),
+ * particles of one cell in their input order.  x must be 16-byte aligned
+ * (its cells are counted in float4 groups; a tensor slice at an odd element
+ * offset is not), v, x_out and v_out 4-byte aligned; neither output may
+ * overlap the other output or an input.  Limits: 1 <= n <= 2^32 - 1,
+ * 1 <= ncell <= PIC_NCELL_MAX, L finite and > 0.  Any violation returns
+ * PIC_EINVAL from checks on the host, before anything is enqueued; larger n
+ * only uses fewer, longer chunks to keep the tables inside the array.
+ * Enqueued on `stream`, asynchronous; the call reports no device-side error
+ * (its one device check, on the scatter's destination index, can fail only
+ * if another writer changes x while the sort runs).  The first call on a
+ * device looks up the array's device address with that device current: make
+ * it before any stream capture.  That address belongs to the device's primary
+ * context and does not survive cudaDeviceReset: do not call this entry point
+ * again in a process after a reset.  Every call shares the array and leaves
+ * its contents behind (each call rewrites its tables in full and clears the
+ * error word first); calls whose work overlaps on the GPU race on it. */
 #define PIC_SORT_NOALLOC_SCRATCH (4u << 20)
 int pic_sort_noalloc(const float *x, const float *v, float *x_out, float *v_out, int64_t n,
                      int32_t ncell, double length, void *stream);

@@ -70,7 +70,6 @@ def _load():
             lib = C.CDLL(build())
             sig = {
                 "orc_particle_mass": (C.c_double, [_P]),
-                "orc_cell_centres": (None, [_P, _D]),
                 "orc_deposit": (C.c_int, [_P, _D, _D]),
                 "orc_field_solve": (C.c_int, [_P, _D, _D, _D]),
                 "orc_field_cg": (C.c_int, [_P, _D, C.c_int, _D, _D]),
@@ -93,6 +92,13 @@ def _load():
                                                     C.c_int64, _F, _L]),
                 "orc_rho_from_fixed": (None, [_P, _L, _D]),
                 "orc_fix_bits": (C.c_int, []),
+                "orc_splitmix64": (C.c_uint64, [C.c_uint64, C.c_uint64]),
+                "orc_load_two_stream": (C.c_int, [C.c_int64, C.c_double, C.c_double,
+                                                  C.c_double, C.c_uint64, C.c_int,
+                                                  C.POINTER(C.c_int32), _D, _D, _D, _D]),
+                "orc_phase_space": (C.c_int, [C.c_int32, C.c_int32, C.c_double,
+                                              C.c_double, C.c_double, C.c_int64, _F, _F,
+                                              C.POINTER(C.c_uint32)]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -164,12 +170,6 @@ class State:
 
 def particle_mass(p: Params) -> float:
     return _load().orc_particle_mass(C.byref(p))
-
-
-def cell_centres(p: Params) -> np.ndarray:
-    xg = np.zeros(p.ng)
-    _load().orc_cell_centres(C.byref(p), _d(xg))
-    return xg
 
 
 def deposit(p: Params, x) -> np.ndarray:
@@ -272,3 +272,37 @@ def rho_from_fixed(p: Params, rho_q) -> np.ndarray:
     rho = np.zeros(p.ng)
     _load().orc_rho_from_fixed(C.byref(p), rho_q.ctypes.data_as(_L), _d(rho))
     return rho
+
+
+def splitmix64(seed: int, k: int) -> int:
+    """Output k >= 1 of SplitMix64 seeded with `seed` (its published definition)."""
+    return int(_load().orc_splitmix64(int(seed) & (2**64 - 1), int(k) & (2**64 - 1)))
+
+
+def load_two_stream(n: int, lx: float, v0: float, vth: float, seed: int, modes=()):
+    """The counter-based two-stream loading (Sec. 2 set-up, Sec. 4 beams,
+    reading R6) in float64: lattice positions displaced by the density modes
+    [(m, eps, phase), ...], beams +-v0 by parity, Box-Muller spread from
+    SplitMix64 outputs 2j+1 and 2j+2.  Returns float64 (x, v)."""
+    nm = len(modes)
+    mode = (C.c_int32 * max(nm, 1))(*[int(m) for m, _, _ in modes])
+    eps = np.array([float(e) for _, e, _ in modes] or [0.0])
+    ph = np.array([float(f) for _, _, f in modes] or [0.0])
+    x = np.zeros(int(n))
+    v = np.zeros(int(n))
+    _check(_load().orc_load_two_stream(int(n), float(lx), float(v0), float(vth),
+                                       int(seed) & (2**64 - 1), nm, mode, _d(eps), _d(ph),
+                                       _d(x), _d(v)), "load")
+    return x, v
+
+
+def phase_space(nx: int, nv: int, lx: float, vmin: float, vmax: float, x32, v32) -> np.ndarray:
+    """Counts of the float32 bin rule of the phase-space snapshot (Sec. 4,
+    Fig. 1), shape (nv, nx): row iv, column ix."""
+    x32 = np.ascontiguousarray(x32, dtype=np.float32)
+    v32 = np.ascontiguousarray(v32, dtype=np.float32)
+    out = np.zeros((int(nv), int(nx)), dtype=np.uint32)
+    _check(_load().orc_phase_space(int(nx), int(nv), float(lx), float(vmin), float(vmax),
+                                   x32.size, x32.ctypes.data_as(_F), v32.ctypes.data_as(_F),
+                                   out.ctypes.data_as(C.POINTER(C.c_uint32))), "phase space")
+    return out

@@ -12,13 +12,15 @@
  *   Sec. 2.1, Eqs. 2-3     leapfrog mover (position, velocity)
  *   Sec. 2.2, Eqs. 6-7     finite-difference Poisson, central-difference E
  *   Sec. 2.3               linear (two-cell) charge and field interpolation
- *   Appendix A             the periodic wrap, cell centres, the CG solver,
- *                          the cycle order
+ *   Appendix A             the periodic wrap, the CG solver, the cycle
+ *                          order, the lattice ("quiet start") loading
+ *   Sec. 4, Fig. 1         the two-stream beams and the phase-space
+ *                          snapshot counts
  * Equation numbers count the displayed lines of Sec. 2: Eq. 1 equation of
  * motion, Eqs. 2-3 leapfrog, Eq. 4 Poisson, Eq. 5 E = -dPhi/dx, Eq. 6
  * discrete Poisson, Eq. 7 discrete E.
  *
- * Readings where the paper is ambiguous (all listed in the design doc):
+ * Readings where the paper is ambiguous:
  *   R1  field solve: the converged solution of Eq. 6 with Phi_0 = 0 (the
  *       listing's CG with 150 fixed iterations is kept as orc_field_cg);
  *   R2  weights: the listing's cell-centred linear weighting, not the
@@ -27,7 +29,9 @@
  *   R5  fixed-point deposit (orc_deposit_fixed): the build's exact integer
  *       form of the Sec. 2.3 weighting, stated at the function;
  *   R13 nearest-grid-point weighting (shape ORC_NGP): the cell xp belongs
- *       to, trunc(xp/dx), takes the whole charge and gives its field.
+ *       to, trunc(xp/dx), takes the whole charge and gives its field;
+ *   R6  loading: beams by particle parity, the thermal spread by Box-Muller
+ *       on a named counter-based generator (orc_load_two_stream).
  *
  * Parity status: every exported function is pinned by a test against
  * something other than itself (closed forms, invariants, brute force, a
@@ -71,13 +75,6 @@ static double orc_q0(const orc_params *p)
 
 /* Particle mass m = Q0 / qoms0. */
 double orc_particle_mass(const orc_params *p) { return orc_q0(p) / p->qoms0; }
-
-/* Cell centres (Appendix A set-up): xg[ic] = dx/2 + dx*ic. */
-void orc_cell_centres(const orc_params *p, double *xg)
-{
-    double dx = orc_dx(p);
-    for (int ic = 0; ic < p->ng; ic++) xg[ic] = dx / 2.0 + dx * ic;
-}
 
 /* Periodic boundary (Appendix A, the wrap in the particle loop), reading R3:
  * x < 0 gains Lx, x >= Lx loses Lx; a negative x so small that x + Lx rounds
@@ -468,3 +465,90 @@ void orc_rho_from_fixed(const orc_params *p, const int64_t *rho_q, double *rho)
 }
 
 int orc_fix_bits(void) { return ORC_FIX_BITS; }
+
+/* ---------------------------------------------------------------------
+ * Initial loading (Sec. 2: positions and velocities sampled from the
+ * problem's distribution; Appendix A set-up: particles on a uniform lattice;
+ * Sec. 4: two beams at +-v0), reading R6, with the counter-based generator
+ * SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom number
+ * generators", OOPSLA 2014) written out from its published definition:
+ * output k >= 1 of the generator seeded with `seed` is the mixing function
+ * applied to seed + k * 0x9E3779B97F4A7C15 (mod 2^64).
+ * --------------------------------------------------------------------- */
+uint64_t orc_splitmix64(uint64_t seed, uint64_t k)
+{
+    uint64_t z = seed + k * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* Particle j of NP (float64 throughout; the library rounds to float32):
+ *   x0 = (j + 1/2) Lx / NP                         the lattice
+ *   x  = x0 - sum_m (eps_m / k_m) sin(k_m x0 + phase_m),  k_m = 2 pi m / Lx,
+ *        folded once into [0, Lx)                  density perturbation
+ *        sum_m eps_m cos(k_m x + phase_m) to first order
+ *   v  = s_j v0 + vth sqrt(-2 ln u1) cos(2 pi u2)  Box-Muller
+ * s_j = +1 for even j, -1 for odd j; u1 = (top 24 bits of z_{2j+1} + 1) 2^-24
+ * in (0, 1], u2 = (top 24 bits of z_{2j+2}) 2^-24 in [0, 1), z_k =
+ * orc_splitmix64(seed, k). */
+int orc_load_two_stream(int64_t np, double lx, double v0, double vth,
+                        uint64_t seed, int nmodes, const int32_t *mode,
+                        const double *eps, const double *phase, double *x,
+                        double *v)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    if (np < 1 || !(lx > 0.0) || nmodes < 0) return ORC_EINVAL;
+    for (int m = 0; m < nmodes; m++)
+        if (mode[m] < 1) return ORC_EINVAL;
+    for (int64_t j = 0; j < np; j++) {
+        double x0 = ((double)j + 0.5) * (lx / (double)np);
+        double xi = 0.0;
+        for (int m = 0; m < nmodes; m++) {
+            double k = two_pi * mode[m] / lx;
+            xi += (eps[m] / k) * sin(k * x0 + phase[m]);
+        }
+        double xj = x0 - xi;
+        if (xj < 0.0) xj += lx;
+        else if (xj >= lx) xj -= lx;
+        uint64_t z1 = orc_splitmix64(seed, 2 * (uint64_t)j + 1);
+        uint64_t z2 = orc_splitmix64(seed, 2 * (uint64_t)j + 2);
+        double u1 = ((double)(z1 >> 40) + 1.0) * ldexp(1.0, -24);
+        double u2 = (double)(z2 >> 40) * ldexp(1.0, -24);
+        double g = sqrt(-2.0 * log(u1)) * cos(two_pi * u2);
+        double s = (j % 2 == 0) ? 1.0 : -1.0;
+        x[j] = xj;
+        v[j] = s * v0 + vth * g;
+    }
+    return ORC_OK;
+}
+
+/* ---------------------------------------------------------------------
+ * Phase-space snapshot (Sec. 4, Fig. 1: the electrons in the (x, v) plane),
+ * as counts of an nx by nv grid of bins over [0, Lx) x [vmin, vmax).  The
+ * bin rule is the library's, stated in float32 so that the counts can be
+ * compared exactly:  sx = (float)(nx / Lx), sv = (float)(nv / (vmax - vmin)),
+ *   ix = min(nx - 1, trunc(x sx)),  iv = floor((v - (float)vmin) sv),
+ * each product and difference one float operation; a particle with x sx not
+ * >= 0 or iv outside [0, nv) is not counted.  counts[iv * nx + ix].
+ * --------------------------------------------------------------------- */
+int orc_phase_space(int32_t nx, int32_t nv, double lx, double vmin,
+                    double vmax, int64_t np, const float *x, const float *v,
+                    uint32_t *counts)
+{
+    if (nx < 1 || nv < 1 || !(lx > 0.0) || !(vmax > vmin)) return ORC_EINVAL;
+    const float sx = (float)((double)nx / lx);
+    const float sv = (float)((double)nv / (vmax - vmin));
+    const float fvmin = (float)vmin;
+    for (int64_t b = 0; b < (int64_t)nx * nv; b++) counts[b] = 0;
+    for (int64_t ip = 0; ip < np; ip++) {
+        float fx = x[ip] * sx;
+        float dv = v[ip] - fvmin;
+        float fv = floorf(dv * sv);
+        if (!(fx >= 0.0f) || !(fv >= 0.0f) || !(fv < (float)nv)) continue;
+        int ix = (int)fx;
+        if (ix > nx - 1) ix = nx - 1;
+        counts[(int64_t)fv * nx + ix] += 1;
+    }
+    return ORC_OK;
+}

@@ -30,8 +30,7 @@ PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA = 0, -1, -2, -3
 PIC_ETIMEOUT, PIC_EDEVICE, PIC_ESTATE = -4, -5, -6
 PIC_FP32_FIXED, PIC_FP32_ATOMIC, PIC_FP64 = 0, 1, 2
 PIC_DEPOSIT_AUTO, PIC_DEPOSIT_ATOMIC, PIC_DEPOSIT_MATCH = 0, 1, 2
-PIC_DEPOSIT_PACKED, PIC_DEPOSIT_MATCH_PACKED, PIC_DEPOSIT_QUAD = 3, 4, 5
-PIC_DEPOSIT_PAIR, PIC_DEPOSIT_QUAD_BULK = 6, 7
+PIC_DEPOSIT_QUAD, PIC_DEPOSIT_PAIR = 5, 6
 PIC_SOLVER_EXACT, PIC_SOLVER_CG = 0, 1
 PIC_SHAPE_CIC, PIC_SHAPE_NGP = 0, 1
 PIC_CG_DEFAULT_ITERATIONS = 150
@@ -40,10 +39,7 @@ PIC_NMODES = 8
 FIX_BITS = 24
 
 VARIANT_NAMES = {PIC_DEPOSIT_ATOMIC: "atomic", PIC_DEPOSIT_MATCH: "match",
-                 PIC_DEPOSIT_PACKED: "packed",
-                 PIC_DEPOSIT_MATCH_PACKED: "match_packed",
-                 PIC_DEPOSIT_QUAD: "quad", PIC_DEPOSIT_PAIR: "pair",
-                 PIC_DEPOSIT_QUAD_BULK: "quad_bulk"}
+                 PIC_DEPOSIT_QUAD: "quad", PIC_DEPOSIT_PAIR: "pair"}
 
 
 class CParams(C.Structure):
@@ -151,6 +147,30 @@ def _ptr(a) -> int:
     return a.data_ptr()
 
 
+def _host_array(a, dtype, n: int, what: str, writable: bool = False):
+    """Check a host argument of n values of `dtype`: a numpy array (converted
+    to a C-contiguous copy of that dtype when reading, required exactly when
+    it is written to) or a contiguous CPU torch tensor of that dtype."""
+    if isinstance(a, np.ndarray):
+        if writable:
+            if a.dtype != dtype or not a.flags["C_CONTIGUOUS"] or not a.flags["WRITEABLE"]:
+                raise TypeError("%s: need a writable C-contiguous %s array" % (what, np.dtype(dtype)))
+        else:
+            a = np.ascontiguousarray(a, dtype=dtype)
+        if a.size != n:
+            raise ValueError("%s: %d values given, %d expected" % (what, a.size, n))
+        return a
+    import torch
+    if not isinstance(a, torch.Tensor):
+        raise TypeError("%s: a numpy array or a CPU torch tensor" % what)
+    want = torch.float64 if np.dtype(dtype) == np.float64 else torch.float32
+    if a.device.type != "cpu" or a.dtype != want or not a.is_contiguous():
+        raise TypeError("%s: need a contiguous CPU torch tensor of %s" % (what, want))
+    if a.numel() != n:
+        raise ValueError("%s: %d values given, %d expected" % (what, a.numel(), n))
+    return a
+
+
 @dataclass
 class Params:
     """Run parameters (pic_params of include/pic.h)."""
@@ -222,14 +242,12 @@ class Run:
         except Exception:
             pass
 
-    def _host(self, a):
-        if isinstance(a, np.ndarray):
-            return np.ascontiguousarray(a, dtype=self.p.dtype)
-        return a  # a contiguous CPU torch tensor of the run's dtype
+    def _host(self, a, what="x", writable=False):
+        return _host_array(a, self.p.dtype, self.p.npart, what, writable)
 
     # --- the C ABI, one method per entry point -------------------------------
     def init(self, x0, v0):
-        x0, v0 = self._host(x0), self._host(v0)
+        x0, v0 = self._host(x0, "x0"), self._host(v0, "v0")
         _check(_lib.pic_init(self._h, _VP(_ptr(x0)), _VP(_ptr(v0))), "pic_init")
 
     def init_loaded(self, ld: Loading):
@@ -237,7 +255,7 @@ class Run:
         _check(_lib.pic_init_loaded(self._h, C.byref(cl)), "pic_init_loaded")
 
     def set_state(self, x, v, step: int):
-        x, v = self._host(x), self._host(v)
+        x, v = self._host(x, "x"), self._host(v, "v")
         _check(_lib.pic_set_state(self._h, _VP(_ptr(x)), _VP(_ptr(v)), int(step)),
                "pic_set_state")
 
@@ -272,10 +290,10 @@ class Run:
         return out
 
     def get_state(self, x=None, v=None):
-        if x is None:
-            x = np.empty(self.p.npart, dtype=self.p.dtype)
-        if v is None:
-            v = np.empty(self.p.npart, dtype=self.p.dtype)
+        x = np.empty(self.p.npart, dtype=self.p.dtype) if x is None else \
+            self._host(x, "x", writable=True)
+        v = np.empty(self.p.npart, dtype=self.p.dtype) if v is None else \
+            self._host(v, "v", writable=True)
         _check(_lib.pic_get_state(self._h, _VP(_ptr(x)), _VP(_ptr(v))), "pic_get_state")
         return x, v
 
@@ -424,8 +442,8 @@ class Pool:
 
     def admit(self, p: Params, x0, v0, steps: int):
         """Slot of the admitted run, or None when the arena or slots are full."""
-        x0 = np.ascontiguousarray(x0, dtype=np.float32) if isinstance(x0, np.ndarray) else x0
-        v0 = np.ascontiguousarray(v0, dtype=np.float32) if isinstance(v0, np.ndarray) else v0
+        x0 = _host_array(x0, np.float32, p.npart, "x0")
+        v0 = _host_array(v0, np.float32, p.npart, "v0")
         slot = C.c_int32(-1)
         cp = p.c()
         rc = _lib.pic_pool_admit(self._h, C.byref(cp), _VP(_ptr(x0)), _VP(_ptr(v0)),
@@ -467,8 +485,8 @@ class Pool:
 
     def get_state(self, slot: int, x=None, v=None):
         n = self.params[slot].npart
-        x = np.empty(n, np.float32) if x is None else x
-        v = np.empty(n, np.float32) if v is None else v
+        x = np.empty(n, np.float32) if x is None else _host_array(x, np.float32, n, "x", True)
+        v = np.empty(n, np.float32) if v is None else _host_array(v, np.float32, n, "v", True)
         _check(_lib.pic_pool_get_state(self._h, int(slot), _VP(_ptr(x)), _VP(_ptr(v))),
                "pic_pool_get_state")
         return x, v

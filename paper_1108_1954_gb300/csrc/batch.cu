@@ -362,7 +362,6 @@ __global__ void __launch_bounds__(512, MINB) pic_batch_kernel(BatchArgs a) {
     Tile tile;
     tile.lo = reinterpret_cast<unsigned *>(smem_raw);
     tile.hi = tile.lo + ngm + 2;
-    tile.packed = nullptr;
     float *sE = reinterpret_cast<float *>(tile.hi + ngm + 2);
     for (;;) {
         if (cl.block_rank() == 0 && threadIdx.x == 0) ex.ticket = (int)atomicAdd(a.next, 1u);

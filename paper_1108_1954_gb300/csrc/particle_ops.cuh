@@ -11,12 +11,6 @@
 namespace pic {
 
 using u64 = unsigned long long;
-constexpr int kMatchPacked = PIC_DEPOSIT_MATCH_PACKED;
-constexpr unsigned long long kPackShift = 40;
-constexpr unsigned long long kPackMask = (1ull << kPackShift) - 1ull;
-// particles a block may pack into one node between flushes
-constexpr int kPackLimit = 65535 - 32;
-
 
 // Cell location of a float32 position by the fixed-point recipe:
 //   s = x*c - 1/2, fl = floor(s), f = s - fl   (float ops, round to nearest)
@@ -102,15 +96,12 @@ __device__ __forceinline__ void push_particle_ngp(float &x, float &v, const floa
 
 // Shared-memory density tiles.  GB300 has no single-instruction 64-bit
 // integer add on shared memory (it runs as a compare-and-swap loop, which
-// serialises badly when the lanes of a warp hit one node), so the unpacked
-// variants keep each node's 64-bit sum as two 32-bit words: a 32-bit
-// fetch-add on the low word, and +1 on the high word from the one add that
-// wraps it.  The packed variants keep one 64-bit word per left node
-// (count << 40 | sum W) and use the 64-bit add.
-// Both tiles are ghost-padded: index j is node (j-1) mod NG, j = 0..NG+1.
+// serialises badly when the lanes of a warp hit one node), so a tile keeps
+// each node's 64-bit sum as two 32-bit words: a 32-bit fetch-add on the low
+// word, and +1 on the high word from the one add that wraps it.  The tile is
+// ghost-padded: index j is node (j-1) mod NG, j = 0..NG+1.
 struct Tile {
-    unsigned *lo, *hi;      // unpacked: 32-bit halves of the node sums
-    u64 *packed;            // packed: one word per left node
+    unsigned *lo, *hi;      // 32-bit halves of the node sums
 };
 
 __device__ __forceinline__ void tile_add(const Tile &t, unsigned j, unsigned val) {
@@ -140,21 +131,15 @@ __device__ __forceinline__ void deposit_one(const Tile &t, float x, bool valid,
             tile_add(t, l.j, kFixOne - W);
             tile_add(t, l.j + 1, W);
         }
-    } else if (VARIANT == PIC_DEPOSIT_PACKED) {
-        if (ok) atomicAdd(&t.packed[l.j], (1ull << kPackShift) | (u64)W);
     } else {
         const unsigned key = ok ? l.j : 0xffffffffu;
         const unsigned peers = __match_any_sync(kFull, key);
         const unsigned wsum = __reduce_add_sync(peers, W);
         if (ok && lane == __ffs(peers) - 1) {
             const unsigned cnt = (unsigned)__popc(peers);
-            if (VARIANT == PIC_DEPOSIT_MATCH) {
-                // cnt * 2^24 - wsum <= 2^29: fits the 32-bit add
-                tile_add(t, l.j, (cnt << kFixBits) - wsum);
-                tile_add(t, l.j + 1, wsum);
-            } else {
-                atomicAdd(&t.packed[l.j], ((u64)cnt << kPackShift) + (u64)wsum);
-            }
+            // cnt * 2^24 - wsum <= 2^29: fits the 32-bit add
+            tile_add(t, l.j, (cnt << kFixBits) - wsum);
+            tile_add(t, l.j + 1, wsum);
         }
     }
 }

@@ -28,6 +28,11 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
+bool is_variant(int v) {
+    return v == PIC_DEPOSIT_ATOMIC || v == PIC_DEPOSIT_MATCH || v == PIC_DEPOSIT_QUAD ||
+           v == PIC_DEPOSIT_PAIR;
+}
+
 }  // namespace
 
 int pic::validate_params(const pic_params *p) {
@@ -38,7 +43,7 @@ int pic::validate_params(const pic_params *p) {
     if (!finite_pos(p->length) || !finite_pos(p->dt) || !finite_pos(p->rho_ion)) return PIC_EINVAL;
     if (!std::isfinite(p->qm) || !(p->qm < 0.0)) return PIC_EINVAL;
     if (p->sort_interval < 0 || p->history < 0) return PIC_EINVAL;
-    if (p->deposit_variant < PIC_DEPOSIT_AUTO || p->deposit_variant > PIC_DEPOSIT_QUAD_BULK) return PIC_EINVAL;
+    if (p->deposit_variant != PIC_DEPOSIT_AUTO && !is_variant(p->deposit_variant)) return PIC_EINVAL;
     if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 1024 || p->block_size % 32)) return PIC_EINVAL;
     if (p->precision == PIC_FP32_FIXED && p->block_size > 512) return PIC_EINVAL;
     if (p->blocks_per_sm < 0 || p->blocks_per_sm > 32) return PIC_EINVAL;
@@ -335,7 +340,6 @@ int read_error_word(pic_run *r) {
     unsigned err = 0;
     PIC_CUDA(cudaMemcpyAsync(&err, &r->dev()->err, sizeof(err), cudaMemcpyDeviceToHost, r->stream));
     PIC_CUDA(cudaStreamSynchronize(r->stream));
-    if (err & kErrTimeout) return PIC_ETIMEOUT;
     if (err & kErrInput) return PIC_EINVAL;
     return err ? PIC_EDEVICE : PIC_OK;
 }
@@ -664,7 +668,7 @@ int pic_set_launch(pic_run *run, int32_t variant, int32_t block, int32_t unroll,
     const int v = variant ? variant : run->variant;
     const int b = block ? block : run->block;
     const int u = unroll ? unroll : run->unroll;
-    if (!ngp && (v < PIC_DEPOSIT_ATOMIC || v > PIC_DEPOSIT_QUAD_BULK || (!fixed && v != PIC_DEPOSIT_ATOMIC)))
+    if (!ngp && (!is_variant(v) || (!fixed && v != PIC_DEPOSIT_ATOMIC)))
         return PIC_EINVAL;
     if (b < 32 || b % 32 || b > (fixed ? 512 : 1024)) return PIC_EINVAL;
     if ((u != 1 && u != 2 && u != 4) || (!fixed && u != 1)) return PIC_EINVAL;
@@ -685,9 +689,8 @@ int pic_autotune(pic_run *run, int32_t reps, pic_tune_entry *results,
     if (!run->ready || run->pending_push) return PIC_ESTATE;
     if (nresults) *nresults = 0;
     if (run->p.precision != PIC_FP32_FIXED) return PIC_OK;
-    static const int variants[] = {PIC_DEPOSIT_ATOMIC, PIC_DEPOSIT_MATCH, PIC_DEPOSIT_PACKED,
-                                   PIC_DEPOSIT_MATCH_PACKED, PIC_DEPOSIT_QUAD, PIC_DEPOSIT_PAIR,
-                                   PIC_DEPOSIT_QUAD_BULK};
+    static const int variants[] = {PIC_DEPOSIT_ATOMIC, PIC_DEPOSIT_MATCH, PIC_DEPOSIT_QUAD,
+                                   PIC_DEPOSIT_PAIR};
     static const int ngp_only[] = {kDepositNgp};
     static const int blocks[] = {128, 256, 512};
     static const int unrolls[] = {1, 2};

@@ -19,7 +19,6 @@ constexpr uint32_t kFixOne = 1u << kFixBits;
 // Bits of the device error word.
 enum : uint32_t {
     kErrPosition = 1u,   // a position outside [0, L) or not finite
-    kErrTimeout = 2u,    // a bounded device wait ran out
     kErrSortKey = 4u,    // a sort key outside the grid
     kErrInput = 8u,      // an uploaded position outside [0, L) (pic_init, pic_set_state)
 };

@@ -15,10 +15,23 @@
 // address; the device address is looked up once per device with
 // cudaGetSymbolAddress (with that device current) on the first call made on
 // it, and reused.  That first call should therefore come before any stream
-// capture.  Every call shares the array and leaves its contents behind; the
+// capture.  The cached address belongs to the device's primary context: it
+// does not survive cudaDeviceReset (or anything else that destroys that
+// context), after which this entry point must not be called again in the
+// process.  Every call shares the array and leaves its contents behind; the
 // counts, offsets and bases are rewritten in full by each call before they
 // are read, and the error word is cleared at the start of each call.  Calls
 // whose work overlaps on the GPU (on different streams) race on the array.
+//
+// Every argument is checked on the host before anything is enqueued: the
+// count pass reads x as float4 groups, so x must be 16-byte aligned (a tensor
+// slice at an odd element offset is not); v, x_out and v_out must be 4-byte
+// aligned; neither output may overlap the other output or an input.  The
+// scatter's bounds check on the destination index can only fail if x changes
+// between the count and the scatter pass (another writer racing on it); the
+// call returns before the kernels run, so such a failure is not reported.
+#include <cmath>
+#include <cstdint>
 #include <mutex>
 
 #include "pic_internal.cuh"
@@ -52,6 +65,14 @@ cudaError_t scratch_address(void **out) {
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
+bool aligned(const void *p, uintptr_t a) { return ((uintptr_t)p % a) == 0; }
+
+// true when the byte ranges [a, a + bytes) and [b, b + bytes) share a byte
+bool overlap(const void *a, const void *b, size_t bytes) {
+    const uintptr_t pa = (uintptr_t)a, pb = (uintptr_t)b;
+    return pa < pb + bytes && pb < pa + bytes;
+}
+
 // Scratch bytes of a sort with nchunk chunks and nseg segments.
 size_t scratch_need(int nchunk, int nseg, int ng) {
     return align256(256) + align256((size_t)nchunk * ng * 4) + align256((size_t)nseg * ng * 4) +
@@ -78,9 +99,15 @@ void geometry(long long n, int nchunk_max, int *nchunk, long long *chunk, int *n
 
 extern "C" int pic_sort_noalloc(const float *x, const float *v, float *x_out, float *v_out,
                                 int64_t n, int32_t ncell, double length, void *stream) {
-    if (!x || !v || !x_out || !v_out || x == x_out || v == v_out) return PIC_EINVAL;
+    if (!x || !v || !x_out || !v_out) return PIC_EINVAL;
     if (n < 1 || n > (int64_t)0xFFFFFFFFll || ncell < 1 || ncell > PIC_NCELL_MAX) return PIC_EINVAL;
-    if (!(length > 0.0)) return PIC_EINVAL;
+    if (!(length > 0.0) || !std::isfinite(length)) return PIC_EINVAL;
+    if (!aligned(x, 16) || !aligned(v, 4) || !aligned(x_out, 4) || !aligned(v_out, 4))
+        return PIC_EINVAL;
+    const size_t bytes = (size_t)n * sizeof(float);
+    if (overlap(x_out, v_out, bytes) || overlap(x_out, x, bytes) || overlap(x_out, v, bytes) ||
+        overlap(v_out, x, bytes) || overlap(v_out, v, bytes))
+        return PIC_EINVAL;
     // the most chunks whose tables fit the scratch array (at most 1024)
     int nchunk = 0, nseg = 0, seg_len = 0;
     long long chunk = 0;

@@ -52,7 +52,8 @@ def test_workspace_size_scales_with_particles(pic):
     dict(dt=0.0), dict(length=float("nan")), dict(length=-1.0),
     dict(rho_ion=0.0), dict(block_size=33), dict(block_size=2048),
     dict(block_size=1024), dict(unroll=3),
-    dict(deposit_variant=9), dict(precision=7), dict(sort_interval=-1),
+    dict(deposit_variant=9), dict(deposit_variant=3), dict(deposit_variant=4),
+    dict(deposit_variant=7), dict(precision=7), dict(sort_interval=-1),
     dict(npart=1 << 33)])
 def test_invalid_parameters_rejected(pic, bad):
     with pytest.raises(pic.PicError) as e:
@@ -124,3 +125,28 @@ def test_pool_table_bytes(pic):
                 (16, 4096, 0, 0, 0, 0)]:
         assert table(*bad)[0] == pic.PIC_EINVAL
     assert pic._lib.pic_pool_table_bytes(None, None) == pic.PIC_EINVAL
+
+
+def test_binding_checks_host_arrays(pic):
+    import numpy as np
+    import torch
+    f = pic._host_array
+    # reading: numpy input is converted, length checked
+    assert f(np.arange(4.0), np.float32, 4, "x").dtype == np.float32
+    with pytest.raises(ValueError):
+        f(np.zeros(5, np.float32), np.float32, 4, "x")
+    # writing: the caller's numpy array must already be the right buffer
+    with pytest.raises(TypeError):
+        f(np.zeros(4, np.float64), np.float32, 4, "x", writable=True)
+    with pytest.raises(TypeError):
+        f(np.zeros(8, np.float32)[::2], np.float32, 4, "x", writable=True)
+    # torch: CPU, contiguous, the run's dtype, the run's length
+    assert f(torch.zeros(4), np.float32, 4, "x") is not None
+    with pytest.raises(TypeError):
+        f(torch.zeros(4, dtype=torch.float64), np.float32, 4, "x")
+    with pytest.raises(TypeError):
+        f(torch.zeros(8)[::2], np.float32, 4, "x")
+    with pytest.raises(ValueError):
+        f(torch.zeros(3), np.float32, 4, "x")
+    with pytest.raises(TypeError):
+        f([0.0] * 4, np.float32, 4, "x")

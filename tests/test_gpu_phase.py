@@ -1,6 +1,7 @@
 """Phase-space snapshots (the Sec. 4 two-stream test, Fig. 1): the device
-histogram against the same bin rule applied to the run's own particles, and
-the paper's observation that the beams mix by t = 20."""
+histogram against the oracle's counts (orc_phase_space, the same float32 bin
+rule) of the run's own particles, and the paper's observation that the beams
+mix by t = 20."""
 import math
 
 import numpy as np
@@ -8,23 +9,11 @@ import pytest
 
 import paper_1108_1954_gb300 as pic  # noqa: E402
 import torch  # noqa: E402,F401
+import oracle as O
 import workloads as W
 
 pytestmark = pytest.mark.gpu
 L4PI = 4.0 * math.pi
-
-
-def host_bins(x, v, nx, nv, L, vmin, vmax):
-    sx = np.float32(nx / L)
-    sv = np.float32(nv / (vmax - vmin))
-    fx = x.astype(np.float32) * sx
-    fv = np.floor((v.astype(np.float32) - np.float32(vmin)) * sv)
-    ok = (fx >= 0) & (fv >= 0) & (fv < nv)
-    ix = np.minimum(fx[ok].astype(np.int64), nx - 1)
-    iv = fv[ok].astype(np.int64)
-    out = np.zeros((nv, nx), dtype=np.uint32)
-    np.add.at(out, (iv, ix), 1)
-    return out
 
 
 @pytest.mark.parametrize("nx,nv", [(64, 64), (128, 100), (1, 1)])
@@ -36,7 +25,7 @@ def test_phase_space_counts(nx, nv):
     run.step_n(7)
     xs, vs = run.get_state()
     got = run.phase_space(nx, nv, -0.5, 0.5)
-    assert np.array_equal(got, host_bins(xs, vs, nx, nv, L4PI, -0.5, 0.5))
+    assert np.array_equal(got, O.phase_space(nx, nv, L4PI, -0.5, 0.5, xs, vs))
     with pytest.raises(pic.PicError):
         run.phase_space(200, 200, -1.0, 1.0)           # above the bin limit
 
@@ -46,7 +35,6 @@ def test_two_stream_beams_mix_by_t20():
     # moved beam particles to velocities near zero.  The slow fraction is a
     # coarse phase-space statistic, so it is compared with the oracle's run
     # from the same state (8.9% of the particles at |v| < 0.1 at step 200).
-    import oracle as O
     n, ng = 20000, 64
     x, v = W.two_stream(n, L4PI, 0.2, 0.01, 11)
     x32, v32 = W.to_f32_state(x, v, L4PI)

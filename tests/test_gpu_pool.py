@@ -165,3 +165,38 @@ def test_pool_rejects_bad_input():
         pool.configure(3, 8, 256)                            # packed variant
     with pytest.raises(pic.PicError):
         pool.configure(2, 1, 32)                             # 64 nodes > 32 threads
+
+
+def test_pool_run_against_the_oracle():
+    """A pooled run checked directly against the FP64 oracle, not only
+    against the single-run path: the density of E^0's set-up and of one step
+    bit for bit against orc_deposit_fixed of the pool's own float32
+    positions, E against the oracle's direct solve of that density, and the
+    step's particles within the one-step tolerances."""
+    import oracle as O
+    from test_gpu_parity import check_field_against_oracle, periodic_dist
+    n, ng, L = 100003, 1024, L4PI
+    modes = W.two_stream_modes_1_to_8(1e-4, 21)
+    x, v = W.two_stream(n, L, 0.2, 0.01, 21, modes=modes)
+    x32, v32 = W.to_f32_state(x, v, L)
+    pool = pic.Pool(max_slots=4, ncell_max=2048, arena_bytes=1 << 28, history=8,
+                    device="cuda:0")
+    # a second run shares the launch
+    xo, vo = W.to_f32_state(*W.two_stream(5003, L, 0.3, 0.02, 22), L)
+    pool.admit(pic.Params(npart=5003, ncell=300, length=L), xo, vo, 1)
+    s = pool.admit(pic.Params(npart=n, ncell=ng, length=L), x32, v32, 1)
+    pool.advance(0)
+    f0 = pool.get_field(s)
+    assert np.array_equal(f0["rho_q"], O.deposit_fixed(ng, L, x32))
+    check_field_against_oracle(f0, n, ng, L)
+    pool.advance(1)
+    x1, v1 = pool.get_state(s)
+    ref = O.State(O.params(ng, n, L, 0.1), x32.astype(np.float64), v32.astype(np.float64))
+    ref.step()
+    assert periodic_dist(x1, ref.x, L).max() <= 1e-5 * L
+    vscale = np.maximum(np.abs(ref.v), 0.2 + 0.01)
+    assert (np.abs(v1 - ref.v) <= 1e-5 * vscale).all()
+    f1 = pool.get_field(s)
+    assert np.array_equal(f1["rho_q"], O.deposit_fixed(ng, L, x1))
+    check_field_against_oracle(f1, n, ng, L)
+    pool.close()

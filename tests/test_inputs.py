@@ -1,32 +1,10 @@
-"""The seeded input generators: the counter-based generator against its
-published test vector, and the statistics of the loadings it feeds."""
+"""The seeded input generators: the draws of the batched ensemble and of the
+request stream."""
 import math
 
 import numpy as np
 
 import workloads as W
-
-
-def test_splitmix64_published_vector():
-    # SplitMix64 (Steele, Lea & Flood 2014), seed 1234567: the reference
-    # implementation's first five outputs
-    got = W.splitmix64(1234567, np.arange(1, 6, dtype=np.uint64)).tolist()
-    assert got == [6457827717110365317, 3203168211198807973, 9817491932198370423,
-                   4593380528125082431, 16408922859458223821]
-
-
-def test_counter_loading_statistics():
-    n, L = 400000, 4 * math.pi
-    x, v = W.counter_two_stream(n, L, 0.2, 0.01, 99, modes=((1, 1e-3, 0.0),))
-    assert x.dtype == np.float32 and (x >= 0).all() and (x < np.float32(L)).all()
-    vp, vm = v[0::2].astype(np.float64), v[1::2].astype(np.float64)
-    se = 0.01 / math.sqrt(n / 2)
-    assert abs(vp.mean() - 0.2) < 5 * se and abs(vm.mean() + 0.2) < 5 * se
-    assert abs(vp.std() / 0.01 - 1.0) < 0.01
-    # the density perturbation of mode 1 has amplitude eps
-    k = 2 * math.pi / L
-    amp = 2 * abs(np.exp(-1j * k * x.astype(np.float64)).mean())
-    assert abs(amp - 1e-3) < 1e-4
 
 
 def test_ensemble_and_request_draws():

@@ -5,8 +5,10 @@ scratch lives in a device array inside the library, shared by every call.
 
 The test calls the entry point through the C ABI on caller-owned device
 buffers, twice in a row with different inputs, and compares each result with
-pic_sort of a run holding the same particles.  A stable sort by cell has one
-answer, so the two must agree bit for bit.  This file is collected last."""
+pic_sort of a run holding the same particles and with numpy's stable argsort
+of the cell keys.  A stable sort by cell has one answer, so all three must
+agree bit for bit.  Bad pointers (misaligned, overlapping) are refused on the
+host before anything is launched.  This file is collected last."""
 import ctypes as C
 import math
 
@@ -37,7 +39,17 @@ def _sorted_by_pic_sort(x, v, ncell):
     return xs, vs
 
 
-def test_noalloc_sort_matches_pic_sort_twice():
+def _stable_argsort_by_cell(x, ncell, length):
+    """The documented key: trunc(x c), c = (float)(NG/L), clamped to [0, NG-1],
+    all in float32; numpy's stable argsort of it."""
+    c = np.float32(ncell / length)
+    u = x.astype(np.float32) * c
+    u = np.where(u > 0, u, np.float32(0))
+    u = np.minimum(u, np.float32(ncell - 1))
+    return np.argsort(u.astype(np.uint32), kind="stable")
+
+
+def test_noalloc_sort_matches_pic_sort_and_argsort_twice():
     fn = _entry()
     stream = torch.cuda.current_stream()
     for call, (n, ncell) in enumerate([(300001, 1024), (2_000_003, 4096)]):
@@ -54,16 +66,48 @@ def test_noalloc_sort_matches_pic_sort_twice():
         assert rc == pic.PIC_OK
         torch.cuda.synchronize()
         xr, vr = _sorted_by_pic_sort(x, v, ncell)
-        assert np.array_equal(xo.cpu().numpy(), xr)
-        assert np.array_equal(vo.cpu().numpy(), vr)
+        got_x, got_v = xo.cpu().numpy(), vo.cpu().numpy()
+        assert np.array_equal(got_x, xr)
+        assert np.array_equal(got_v, vr)
+        order = _stable_argsort_by_cell(x, ncell, L)
+        assert np.array_equal(got_x, x[order])
+        assert np.array_equal(got_v, v[order])
 
 
 def test_noalloc_sort_rejects_sizes_beyond_its_limits():
     fn = _entry()
     xd = torch.zeros(16, dtype=torch.float32, device="cuda")
     xo = torch.zeros(16, dtype=torch.float32, device="cuda")
+    vo = torch.zeros(16, dtype=torch.float32, device="cuda")
     s = torch.cuda.current_stream().cuda_stream
-    assert fn(xd.data_ptr(), xd.data_ptr(), xo.data_ptr(), xo.data_ptr(), 16,
+    assert fn(xd.data_ptr(), xd.data_ptr(), xo.data_ptr(), vo.data_ptr(), 16,
               pic.PIC_NCELL_MAX + 1, L, s) == pic.PIC_EINVAL
-    assert fn(xd.data_ptr(), xd.data_ptr(), xo.data_ptr(), xo.data_ptr(), 0, 64, L, s) == pic.PIC_EINVAL
-    assert fn(xd.data_ptr(), xd.data_ptr(), xd.data_ptr(), xo.data_ptr(), 16, 64, L, s) == pic.PIC_EINVAL
+    assert fn(xd.data_ptr(), xd.data_ptr(), xo.data_ptr(), vo.data_ptr(), 0, 64, L,
+              s) == pic.PIC_EINVAL
+    assert fn(xd.data_ptr(), xd.data_ptr(), xo.data_ptr(), vo.data_ptr(), 16, 64,
+              float("inf"), s) == pic.PIC_EINVAL
+
+
+def test_noalloc_sort_refuses_bad_pointers_on_the_host():
+    """The bad cases are refused by the host checks, so no kernel ever sees them."""
+    fn = _entry()
+    s = torch.cuda.current_stream().cuda_stream
+    buf = torch.zeros(4 * 64, dtype=torch.float32, device="cuda")
+    base = buf.data_ptr()
+    assert base % 16 == 0
+    n = 32
+    x, v, xo, vo = base, base + 4 * 64, base + 8 * 64, base + 12 * 64
+    ok = [x, v, xo, vo]
+    # a position array one element past a 16-byte boundary (a slice x[1:])
+    assert fn(x + 4, v, xo, vo, n, 64, L, s) == pic.PIC_EINVAL
+    # outputs on an input, on each other, or partly overlapping
+    assert fn(x, v, x, vo, n, 64, L, s) == pic.PIC_EINVAL
+    assert fn(x, v, xo, v, n, 64, L, s) == pic.PIC_EINVAL
+    assert fn(x, v, v, x, n, 64, L, s) == pic.PIC_EINVAL
+    assert fn(x, v, xo, xo, n, 64, L, s) == pic.PIC_EINVAL
+    assert fn(x, v, xo, xo + 4 * (n - 1), n, 64, L, s) == pic.PIC_EINVAL
+    # an output at a 4-byte (not 16-byte) boundary is allowed
+    assert fn(x, v, xo + 4, vo, n, 64, L, s) == pic.PIC_OK
+    torch.cuda.synchronize()
+    assert fn(*ok, n, 64, L, s) == pic.PIC_OK
+    torch.cuda.synchronize()

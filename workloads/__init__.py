@@ -8,7 +8,7 @@ verification test (Sec. 4), the run-parameter draws of the batched ensemble
 and the request stream of the serving loop.  It contains none of the step's
 arithmetic (no gather, push, deposit or field solve).
 
-Readings of the paper taken here (each restated in the design doc):
+Readings of the paper taken here:
   * beams are assigned by particle parity (even index +v0, odd -v0), so the
     two beams hold exactly half the particles each; the Appendix A listing
     draws the sign at random, which leaves the beams unequal;
@@ -140,52 +140,6 @@ def to_f32_state(x: np.ndarray, v: np.ndarray, length: float):
     x32[x32 >= np.float32(length)] = np.float32(0.0)
     x32[x32 < 0] = np.float32(0.0)
     return x32, v.astype(np.float32)
-
-
-# --- the counter-based loading of the device loader, restated -----------
-
-_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
-
-
-def splitmix64(seed: int, k: np.ndarray) -> np.ndarray:
-    """k-th outputs (k >= 1) of SplitMix64 seeded with `seed` (Steele, Lea &
-    Flood, OOPSLA 2014): the finaliser of seed + k * 0x9E3779B97F4A7C15."""
-    with np.errstate(over="ignore"):
-        z = np.uint64(seed) + np.asarray(k, dtype=np.uint64) * _GOLDEN
-        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
-        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
-        return z ^ (z >> np.uint64(31))
-
-
-def counter_two_stream(n: int, length: float, v0: float, vth: float, seed: int,
-                       modes=()):
-    """Host restatement of the device loader (pic_load_two_stream): lattice
-    positions displaced by the density modes, beams +-v0 by parity, Box-Muller
-    spread from SplitMix64 outputs 2j+1 and 2j+2.  Float32 where the device
-    computes in float32 (the transcendental functions may differ by an ulp).
-    Returns float32 (x, v)."""
-    j = np.arange(n, dtype=np.float64)
-    x0 = (j + 0.5) * (length / n)
-    x0f = x0.astype(np.float32)
-    disp = np.zeros(n, dtype=np.float32)
-    for m, eps, phase in modes:
-        k = TWO_PI * m / length
-        kf, amp, ph = np.float32(k), np.float32(eps / k), np.float32(phase)
-        disp = (amp * np.sin(kf * x0f + ph) + disp).astype(np.float32)
-    x = x0 - disp.astype(np.float64)
-    x = np.where(x < 0, x + length, np.where(x >= length, x - length, x))
-    xf = x.astype(np.float32)
-    xf[~(xf < np.float32(length))] = 0.0
-    xf[xf < 0] = 0.0
-    kk = np.arange(n, dtype=np.uint64)
-    z1 = splitmix64(seed, np.uint64(2) * kk + np.uint64(1))
-    z2 = splitmix64(seed, np.uint64(2) * kk + np.uint64(2))
-    u1 = ((z1 >> np.uint64(40)) + np.uint64(1)).astype(np.float32) * np.float32(2.0 ** -24)
-    u2 = (z2 >> np.uint64(40)).astype(np.float32) * np.float32(2.0 ** -24)
-    g = np.sqrt(np.float32(-2.0) * np.log(u1)) * np.cos(np.float32(TWO_PI) * u2)
-    s = np.where(np.arange(n) % 2 == 0, np.float32(1.0), np.float32(-1.0))
-    v = (np.float32(vth) * g.astype(np.float32) + s * np.float32(v0)).astype(np.float32)
-    return xf, v
 
 
 # --- batched ensemble and request stream ---------------------------------
