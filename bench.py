@@ -508,12 +508,12 @@ def variant_scan(args):
     for checkpoint in (0, 200, 600):
         while run.step < checkpoint:
             run.step_n(min(100, checkpoint - run.step))
-        xs, vs = run.get_state()
+        xs, vs = run.get_cells()
         st = run.step
         row = {"step": st}
         for var in (1, 2, 5, 6):
             for blk, un in ((512, 1), (512, 2), (256, 1)):
-                run.set_state(xs, vs, st)
+                run.set_cells(xs, vs, st)
                 run.set_launch(var, blk, un)
                 ev = [(torch.cuda.Event(True), torch.cuda.Event(True)) for _ in range(2 * S)]
                 for a, b in ev:
@@ -526,7 +526,7 @@ def variant_scan(args):
                 torch.cuda.synchronize()
                 row["%d/%d/%d" % (var, blk, un)] = round(float(np.mean(
                     [a.elapsed_time(b) for a, b in ev])), 4)
-        run.set_state(xs, vs, st)
+        run.set_cells(xs, vs, st)
         out.append(row)
     run.close()
     return out

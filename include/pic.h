@@ -19,9 +19,18 @@
  * particle (below), so the density is the same integer for any launch shape
  * or particle order; the field solve and all diagnostics are float64.
  *
+ * Cell units.  In the float32 modes the device keeps each position as its
+ * cell coordinate u = x NG / L in [0, NG) (node g at u = g + 1/2), so the box
+ * is exactly [0, NG) and the drift is u += v (float)(dt NG/L).  Positions
+ * cross the ABI in physical units and are converted on the device, each
+ * conversion one rounding of a float64 product:
+ *   in   u = (float)((double)x (NG/L)), a u rounding to NG is 0;
+ *   out  x = (float)((double)u (L/NG)), at most the float below (float)L.
+ * pic_get_cells / pic_set_cells exchange u itself (exact checkpoints).
+ *
  * Fixed-point deposit (the library's exact form of the Sec. 2.3 weighting).
- * With c = (float)(NG / L) and float operations rounded to nearest:
- *   u = x*c, s = u - 0.5f, i = floorf(s), f = s - i, W = trunc(f * 2^24);
+ * With float operations rounded to nearest:
+ *   s = u - 0.5f, i = floorf(s), f = s - i, W = trunc(f * 2^24);
  *   rho_q[(i+1) mod NG] += W,  rho_q[i mod NG] += 2^24 - W.
  * The float64 density is rho_g = rho_ion - rho_ion (NG/N) rho_q[g] 2^-24.
  *
@@ -242,12 +251,22 @@ int pic_diagnostics(pic_run *run, int64_t first, int32_t count,
 int64_t pic_step_count(const pic_run *run);
 
 /* Copy x^n, v^{n-1/2} (N values each, run precision) to host arrays, in the
- * current particle order.  Synchronises. */
+ * current particle order; float32 positions are converted from cell units
+ * (above) in the run's idle particle buffer.  Synchronises. */
 int pic_get_state(pic_run *run, void *x, void *v);
 
 /* Replace x, v with host arrays (a checkpoint restore) and set the step
  * counter to `step`; re-deposits and re-solves like pic_init. Synchronises. */
 int pic_set_state(pic_run *run, const void *x, const void *v, int64_t step);
+
+/* The float32 modes' state exactly as the device holds it: u^n (cell
+ * coordinates, N float) and v^{n-1/2} (N float), in the current particle
+ * order.  pic_set_cells restores such a state (u must lie in [0, NG), else
+ * PIC_EINVAL as for pic_init) and sets the step counter; together they make
+ * a checkpoint that continues bit for bit.  PIC_EINVAL for PIC_FP64 runs.
+ * Synchronise. */
+int pic_get_cells(pic_run *run, float *u, void *v);
+int pic_set_cells(pic_run *run, const float *u, const void *v, int64_t step);
 
 /* Copy the grid of the last solve to host arrays (any may be NULL):
  * rho[NG], phi[NG], E[NG] float64 and rho_q[NG] (the fixed-point sums that
@@ -257,16 +276,19 @@ int pic_get_field(pic_run *run, double *rho, double *phi, double *E,
 
 /* Phase-space histogram f(x, v) of the current particles (the (x, v)
  * snapshots of the Sec. 4 two-stream test, Fig. 1): counts[iv * nx + ix] (host,
- * nx * nv uint32) of the particles with ix = min(nx - 1, trunc(x * (nx/L))) and
- * iv = floor((v - vmin) * (nv/(vmax - vmin))), both scale factors and the
- * products in float32; particles with iv outside [0, nv) are not counted.
+ * nx * nv uint32) of the particles with ix = min(nx - 1, trunc(p * sx)) and
+ * iv = floor((v - vmin) * (nv/(vmax - vmin))), the scale factors, the
+ * difference and the products in float32, where p is the stored position:
+ * the cell coordinate u with sx = nx/NG in the float32 modes, x with
+ * sx = nx/L in PIC_FP64.  Particles with iv outside [0, nv) are not counted.
  * nx * nv <= PIC_PHASE_MAX_BINS, vmax > vmin, else PIC_EINVAL.  Synchronises. */
 #define PIC_PHASE_MAX_BINS 16384
 int pic_phase_space(pic_run *run, int32_t nx, int32_t nv, double vmin, double vmax,
                     uint32_t *counts);
 
 /* Device pointers of the current particle arrays (they alternate after each
- * sort) and of the float32 field used by the gather. */
+ * sort; positions in cell units in the float32 modes) and of the float32
+ * field used by the gather. */
 int pic_device_arrays(pic_run *run, void **x, void **v, void **E32);
 
 /* The launch shape the run uses for its fused push (any pointer may be
@@ -393,8 +415,12 @@ int pic_pool_finished(const pic_pool *pool, int32_t *slots, int32_t max, int32_t
 /* Steps done by the run in `slot`. */
 int pic_pool_step_count(const pic_pool *pool, int32_t slot, int64_t *step);
 
-/* Results of a run (synchronise): state, field of its last step, history. */
+/* Results of a run (synchronise): state (positions converted from cell
+ * units on the host, by the same two float64-rounded steps as pic_get_state),
+ * the state in cell units as held on the device, field of its last step,
+ * history. */
 int pic_pool_get_state(pic_pool *pool, int32_t slot, void *x, void *v);
+int pic_pool_get_cells(pic_pool *pool, int32_t slot, float *u, float *v);
 int pic_pool_get_field(pic_pool *pool, int32_t slot, double *rho, double *phi, double *E,
                        int64_t *rho_q);
 int pic_pool_diagnostics(pic_pool *pool, int32_t slot, int64_t first, int32_t count,

@@ -86,10 +86,8 @@ def _load():
                                       C.c_int, _D, _D]),
                 "orc_field_energy": (C.c_double, [_P, _D]),
                 "orc_mode_amplitudes": (None, [_P, _D, C.c_int, _D]),
-                "orc_deposit_fixed": (C.c_int, [C.c_int32, C.c_double,
-                                                C.c_int64, _F, _L]),
-                "orc_deposit_fixed_ngp": (C.c_int, [C.c_int32, C.c_double,
-                                                    C.c_int64, _F, _L]),
+                "orc_deposit_fixed": (C.c_int, [C.c_int32, C.c_int64, _F, _L]),
+                "orc_deposit_fixed_ngp": (C.c_int, [C.c_int32, C.c_int64, _F, _L]),
                 "orc_rho_from_fixed": (None, [_P, _L, _D]),
                 "orc_fix_bits": (C.c_int, []),
                 "orc_splitmix64": (C.c_uint64, [C.c_uint64, C.c_uint64]),
@@ -245,23 +243,23 @@ def mode_amplitudes(p: Params, E, nmodes: int = 8) -> np.ndarray:
     return amp
 
 
-def deposit_fixed(ng: int, lx: float, x32) -> np.ndarray:
-    """Fixed-point deposit of float32 positions (reading R5): int64 rho_q."""
-    x32 = np.ascontiguousarray(x32, dtype=np.float32)
+def deposit_fixed(ng: int, u32) -> np.ndarray:
+    """Fixed-point deposit (reading R5) of float32 cell coordinates
+    u = x/dx: int64 rho_q."""
+    u32 = np.ascontiguousarray(u32, dtype=np.float32)
     rho_q = np.zeros(int(ng), dtype=np.int64)
-    _check(_load().orc_deposit_fixed(int(ng), float(lx), x32.size,
-                                     x32.ctypes.data_as(_F),
+    _check(_load().orc_deposit_fixed(int(ng), u32.size, u32.ctypes.data_as(_F),
                                      rho_q.ctypes.data_as(_L)),
            "fixed deposit")
     return rho_q
 
 
-def deposit_fixed_ngp(ng: int, lx: float, x32) -> np.ndarray:
-    """Fixed-point nearest-grid-point deposit of float32 positions (R13)."""
-    x32 = np.ascontiguousarray(x32, dtype=np.float32)
+def deposit_fixed_ngp(ng: int, u32) -> np.ndarray:
+    """Fixed-point nearest-grid-point deposit (R13) of float32 cell
+    coordinates."""
+    u32 = np.ascontiguousarray(u32, dtype=np.float32)
     rho_q = np.zeros(int(ng), dtype=np.int64)
-    _check(_load().orc_deposit_fixed_ngp(int(ng), float(lx), x32.size,
-                                         x32.ctypes.data_as(_F),
+    _check(_load().orc_deposit_fixed_ngp(int(ng), u32.size, u32.ctypes.data_as(_F),
                                          rho_q.ctypes.data_as(_L)),
            "fixed NGP deposit")
     return rho_q

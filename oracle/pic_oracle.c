@@ -400,9 +400,9 @@ void orc_mode_amplitudes(const orc_params *p, const double *E, int nmodes,
 /* ---------------------------------------------------------------------
  * Fixed-point deposit, reading R5 (not in the paper; the build's exact form
  * of the Sec. 2.3 linear weighting, so that a density summed in any order is
- * the same integer).  For each float32 position x:
- *   c = (float)(NG / Lx)            (the quotient formed in double)
- *   u = x * c;  s = u - 0.5f;  fl = floorf(s);  f = s - fl
+ * the same integer).  The library keeps a float32 position as its cell
+ * coordinate u = xp/dx in [0, NG) (node ic at u = ic + 1/2).  For each u:
+ *   s = u - 0.5f;  fl = floorf(s);  f = s - fl
  *                                   (single float operations, round to nearest)
  *   i = (int)fl                     (left node, -1 .. NG-1)
  *   W = (uint32) trunc(f * 2^24)    (the right node's share, 0 .. 2^24)
@@ -412,15 +412,12 @@ void orc_mode_amplitudes(const orc_params *p, const double *E, int nmodes,
  * --------------------------------------------------------------------- */
 #define ORC_FIX_BITS 24
 
-int orc_deposit_fixed(int32_t ng, double lx, int64_t np, const float *x,
-                      int64_t *rho_q)
+int orc_deposit_fixed(int32_t ng, int64_t np, const float *u, int64_t *rho_q)
 {
-    const float c = (float)((double)ng / lx);
     const float scale = 16777216.0f; /* 2^24 */
     for (int g = 0; g < ng; g++) rho_q[g] = 0;
     for (int64_t ip = 0; ip < np; ip++) {
-        float u = x[ip] * c;
-        float s = u - 0.5f;
+        float s = u[ip] - 0.5f;
         float fl = floorf(s);
         float f = s - fl;
         if (!(fl >= -1.0f && fl <= (float)ng)) return ORC_ERANGE;
@@ -434,18 +431,14 @@ int orc_deposit_fixed(int32_t ng, double lx, int64_t np, const float *x,
     return ORC_OK;
 }
 
-/* The fixed-point form of the nearest-grid-point weighting (reading R13):
- *   u = x * c  (one float multiplication, round to nearest),
- *   i = (int)floorf(u), cell NG (x rounding up to the box end) is cell 0,
- *   rho_q[i] += 2^24. */
-int orc_deposit_fixed_ngp(int32_t ng, double lx, int64_t np, const float *x,
-                          int64_t *rho_q)
+/* The fixed-point form of the nearest-grid-point weighting (reading R13) on
+ * cell coordinates: i = (int)floorf(u), cell NG (a coordinate at the box
+ * end) is cell 0, rho_q[i] += 2^24. */
+int orc_deposit_fixed_ngp(int32_t ng, int64_t np, const float *u, int64_t *rho_q)
 {
-    const float c = (float)((double)ng / lx);
     for (int g = 0; g < ng; g++) rho_q[g] = 0;
     for (int64_t ip = 0; ip < np; ip++) {
-        float u = x[ip] * c;
-        float fl = floorf(u);
+        float fl = floorf(u[ip]);
         if (!(fl >= 0.0f && fl <= (float)ng)) return ORC_ERANGE;
         int i = (int)fl;
         if (i == ng) i = 0;

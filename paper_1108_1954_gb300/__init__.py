@@ -90,6 +90,9 @@ _SIG = {
     "pic_get_state": (C.c_int, [_VP, _VP, _VP]),
     "pic_set_state": (C.c_int, [_VP, _VP, _VP, C.c_int64]),
     "pic_get_field": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "pic_get_cells": (C.c_int, [_VP, _VP, _VP]),
+    "pic_set_cells": (C.c_int, [_VP, _VP, _VP, C.c_int64]),
+    "pic_pool_get_cells": (C.c_int, [_VP, C.c_int32, _VP, _VP]),
     "pic_device_arrays": (C.c_int, [_VP, C.POINTER(_VP), C.POINTER(_VP),
                                     C.POINTER(_VP)]),
     "pic_launch_shape": (C.c_int, [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
@@ -297,6 +300,21 @@ class Run:
         _check(_lib.pic_get_state(self._h, _VP(_ptr(x)), _VP(_ptr(v))), "pic_get_state")
         return x, v
 
+    def get_cells(self, u=None, v=None):
+        """The float32 state as the device holds it: (u, v), u = x NG/L."""
+        n = self.p.npart
+        u = np.empty(n, np.float32) if u is None else _host_array(u, np.float32, n, "u", True)
+        v = np.empty(n, np.float32) if v is None else _host_array(v, np.float32, n, "v", True)
+        _check(_lib.pic_get_cells(self._h, _VP(_ptr(u)), _VP(_ptr(v))), "pic_get_cells")
+        return u, v
+
+    def set_cells(self, u, v, step: int):
+        """Restore a state from get_cells (continues bit for bit)."""
+        u = _host_array(u, np.float32, self.p.npart, "u")
+        v = _host_array(v, np.float32, self.p.npart, "v")
+        _check(_lib.pic_set_cells(self._h, _VP(_ptr(u)), _VP(_ptr(v)), int(step)),
+               "pic_set_cells")
+
     def get_field(self):
         ng = self.p.ncell
         rho, phi, E = np.zeros(ng), np.zeros(ng), np.zeros(ng)
@@ -313,7 +331,8 @@ class Run:
         return out
 
     def device_arrays(self):
-        """Torch views (x, v, E32) of the current device arrays."""
+        """Torch views (x, v, E32) of the current device arrays (positions in
+        cell units in the float32 modes)."""
         import torch
         x, v, e = _VP(), _VP(), _VP()
         _check(_lib.pic_device_arrays(self._h, C.byref(x), C.byref(v), C.byref(e)),
@@ -490,6 +509,14 @@ class Pool:
         _check(_lib.pic_pool_get_state(self._h, int(slot), _VP(_ptr(x)), _VP(_ptr(v))),
                "pic_pool_get_state")
         return x, v
+
+    def get_cells(self, slot: int):
+        """(u, v) of the run in `slot` as the device holds them."""
+        n = self.params[slot].npart
+        u, v = np.empty(n, np.float32), np.empty(n, np.float32)
+        _check(_lib.pic_pool_get_cells(self._h, int(slot), _VP(_ptr(u)), _VP(_ptr(v))),
+               "pic_pool_get_cells")
+        return u, v
 
     def get_field(self, slot: int):
         ng = self.params[slot].ncell

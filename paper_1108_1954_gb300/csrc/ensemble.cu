@@ -304,10 +304,9 @@ int admit_common(pic_pool *pool, const pic_params *p, int64_t steps, int32_t *sl
     d.v = (float *)(base + L.v);
     d.n = p->npart;
     d.pc.ng = p->ncell;
-    d.pc.inv_dx = (float)((double)p->ncell / p->length);
-    d.pc.length = (float)p->length;
+    d.pc.ngf = (float)p->ncell;
+    d.pc.kdrift = (float)(p->dt * (double)p->ncell / p->length);
     d.pc.qmdt = (float)(p->qm * p->dt);
-    d.pc.dt = (float)p->dt;
     d.E32 = (float *)(base + L.E32);
     d.E64 = (double *)(base + L.E64);
     d.phi = (double *)(base + L.phi);
@@ -373,6 +372,9 @@ int pic_pool_admit(pic_pool *pool, const pic_params *p, const void *x0, const vo
     const size_t pb = (size_t)p->npart * 4;
     cudaError_t e = cudaMemcpyAsync(d.x, x0, pb, cudaMemcpyHostToDevice, pool->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d.v, v0, pb, cudaMemcpyHostToDevice, pool->stream);
+    if (e == cudaSuccess)
+        e = launch_to_cells(d.x, p->npart, (double)p->ncell / p->length, (float)p->ncell, Lf,
+                            pool->d_err(), pool->sms, pool->stream);
     if (e != cudaSuccess) { drop_slot(pool, s); return cuda_fail(e); }
     *slot = s;
     return PIC_OK;
@@ -393,6 +395,9 @@ int pic_pool_admit_loaded(pic_pool *pool, const pic_params *p, const pic_loading
     a.x = pool->slots[s].desc.x;
     a.v = pool->slots[s].desc.v;
     cudaError_t e = launch_load(a, pool->sms, pool->stream);
+    if (e == cudaSuccess)
+        e = launch_to_cells(a.x, p->npart, (double)p->ncell / p->length, (float)p->ncell,
+                            (float)p->length, pool->d_err(), pool->sms, pool->stream);
     if (e != cudaSuccess) { drop_slot(pool, s); return cuda_fail(e); }
     *slot = s;
     return PIC_OK;
@@ -456,14 +461,30 @@ int pic_pool_step_count(const pic_pool *pool, int32_t slot, int64_t *step) {
     return PIC_OK;
 }
 
-int pic_pool_get_state(pic_pool *pool, int32_t slot, void *x, void *v) {
+int pic_pool_get_cells(pic_pool *pool, int32_t slot, float *u, float *v) {
     if (!slot_ok(pool, slot)) return PIC_EINVAL;
     const pic_pool::Slot &sl = pool->slots[slot];
     if (sl.needs_init) return PIC_ESTATE;
     const size_t pb = (size_t)sl.p.npart * 4;
-    if (x) PIC_CUDA(cudaMemcpyAsync(x, sl.desc.x, pb, cudaMemcpyDeviceToHost, pool->stream));
+    if (u) PIC_CUDA(cudaMemcpyAsync(u, sl.desc.x, pb, cudaMemcpyDeviceToHost, pool->stream));
     if (v) PIC_CUDA(cudaMemcpyAsync(v, sl.desc.v, pb, cudaMemcpyDeviceToHost, pool->stream));
     return read_error(pool);
+}
+
+int pic_pool_get_state(pic_pool *pool, int32_t slot, void *x, void *v) {
+    int rc = pic_pool_get_cells(pool, slot, (float *)x, (float *)v);
+    if (rc || !x) return rc;
+    // cell coordinates to physical positions on the host, with the same two
+    // float64-rounded steps as the device conversion of a single run
+    const pic_pool::Slot &sl = pool->slots[slot];
+    const double to_phys = sl.p.length / (double)sl.p.ncell;
+    const float top = below((float)sl.p.length);
+    float *xf = (float *)x;
+    for (int64_t i = 0; i < sl.p.npart; i++) {
+        const float xi = (float)((double)xf[i] * to_phys);
+        xf[i] = xi > top ? top : xi;
+    }
+    return PIC_OK;
 }
 
 int pic_pool_get_field(pic_pool *pool, int32_t slot, double *rho, double *phi, double *E,

@@ -12,8 +12,8 @@ namespace pic {
 
 using u64 = unsigned long long;
 
-// Cell location of a float32 position by the fixed-point recipe:
-//   s = x*c - 1/2, fl = floor(s), f = s - fl   (float ops, round to nearest)
+// Cell location of a float32 cell coordinate u (the fixed-point recipe):
+//   s = u - 1/2, fl = floor(s), f = s - fl   (float ops, round to nearest)
 // floor(s) is formed as (s + 1.5*2^23 rounded down) - 1.5*2^23, which equals
 // floorf(s) exactly for |s| < 2^22 (NG <= 8192; checked for every float in
 // [-1, 8193]) and runs on the FMA pipe instead of the conversion unit; the
@@ -30,9 +30,9 @@ struct Loc {
 constexpr float kMagic = 12582912.0f;          // 1.5 * 2^23
 constexpr int kMagicBitsMinus1 = 0x4B400000 - 1;
 
-__device__ __forceinline__ Loc locate(float x, float inv_dx) {
+__device__ __forceinline__ Loc locate(float u) {
     Loc l;
-    const float s = __fsub_rn(__fmul_rn(x, inv_dx), 0.5f);
+    const float s = __fsub_rn(u, 0.5f);
     const float t = __fadd_rd(s, kMagic);
     const float fl = __fsub_rn(t, kMagic);
     l.f = __fsub_rn(s, fl);
@@ -45,53 +45,53 @@ __device__ __forceinline__ unsigned fixed_weight(float f) {
     return __float2uint_rz(__fmul_rn(f, 16777216.0f));
 }
 
-// Kick (Eq. 3), drift (Eq. 2) and wrap of one particle, given the field ep
-// at the particle; accumulates v_old v_new and v_new.
-__device__ __forceinline__ void kick_drift_wrap(float &x, float &v, float ep, const PushConsts &c,
+// Kick (Eq. 3), drift (Eq. 2, in cell units: u advances by v dt NG/L) and
+// the periodic wrap to [0, NG) of one particle, given the field ep at the
+// particle; accumulates v_old v_new and v_new.
+__device__ __forceinline__ void kick_drift_wrap(float &u, float &v, float ep, const PushConsts &c,
                                                 float &ke, float &mom) {
     const float vn = fmaf(c.qmdt, ep, v);
     ke = fmaf(v, vn, ke);
     mom += vn;
-    float xn = fmaf(vn, c.dt, x);
-    xn = xn < 0.0f ? xn + c.length : xn;
-    xn = xn >= c.length ? xn - c.length : xn;
-    xn = xn >= c.length ? 0.0f : xn;   // x + L rounded up to L: the point 0
-    x = xn;
+    float un = fmaf(vn, c.kdrift, u);
+    un = un < 0.0f ? un + c.ngf : un;
+    un = un >= c.ngf ? un - c.ngf : un;
+    un = un >= c.ngf ? 0.0f : un;      // u + NG rounded up to NG: the point 0
+    u = un;
     v = vn;
 }
 
 // Gather (left and right node), kick, drift, wrap.
 // sE[j] = E_{(j-1) mod NG} for j = 0..NG+1 (ghost-padded).
-__device__ __forceinline__ void push_particle(float &x, float &v, const float *sE,
+__device__ __forceinline__ void push_particle(float &u, float &v, const float *sE,
                                               const PushConsts &c, float &ke,
                                               float &mom) {
-    const Loc l = locate(x, c.inv_dx);
+    const Loc l = locate(u);
     const bool ok = l.j <= (unsigned)c.ng;
     const unsigned j = ok ? l.j : 0u;
     const float e0 = sE[j], e1 = sE[j + 1];
     const float ep = ok ? fmaf(l.f, e1 - e0, e0) : 0.0f;
-    kick_drift_wrap(x, v, ep, c, ke, mom);
+    kick_drift_wrap(u, v, ep, c, ke, mom);
 }
 
 // Nearest-grid-point weighting (PIC_SHAPE_NGP; Sec. 2: a grid point's density
 // counts the particles of its cell, and a particle feels its cell's field):
-// with nodes at the cell centres the cell of x is floor(x * c), formed by the
+// with nodes at the cell centres the cell of u is floor(u), formed by the
 // same rounded-down magic sum as locate (exact on [-1, 8193]).  Returns the
-// ghost-padded tile index j = cell + 1 (cell NG, a position rounding up to
-// the box end, is j = NG + 1, the ghost of node 0); a valid position has
-// j - 1 in [0, NG] (one unsigned test).
-__device__ __forceinline__ unsigned locate_ngp(float x, float inv_dx) {
-    const float t = __fadd_rd(__fmul_rn(x, inv_dx), kMagic);
+// ghost-padded tile index j = cell + 1; a valid position has j - 1 in
+// [0, NG] (one unsigned test).
+__device__ __forceinline__ unsigned locate_ngp(float u) {
+    const float t = __fadd_rd(u, kMagic);
     return (unsigned)(__float_as_int(t) - kMagicBitsMinus1);
 }
 
-__device__ __forceinline__ void push_particle_ngp(float &x, float &v, const float *sE,
+__device__ __forceinline__ void push_particle_ngp(float &u, float &v, const float *sE,
                                                   const PushConsts &c, float &ke,
                                                   float &mom) {
-    const unsigned j = locate_ngp(x, c.inv_dx);
+    const unsigned j = locate_ngp(u);
     const bool ok = j - 1u <= (unsigned)c.ng;
     const float ep = ok ? sE[j] : 0.0f;
-    kick_drift_wrap(x, v, ep, c, ke, mom);
+    kick_drift_wrap(u, v, ep, c, ke, mom);
 }
 
 // Shared-memory density tiles.  GB300 has no single-instruction 64-bit
@@ -115,13 +115,13 @@ template <int VARIANT>
 __device__ __forceinline__ void deposit_one(const Tile &t, float x, bool valid,
                                             const PushConsts &c, unsigned *err, int lane) {
     if (VARIANT == kDepositNgp) {
-        const unsigned j = locate_ngp(x, c.inv_dx);
+        const unsigned j = locate_ngp(x);
         const bool ok = valid && j - 1u <= (unsigned)c.ng;
         if (valid && !ok) atomicOr(err, kErrPosition);
         if (ok) tile_add(t, j, kFixOne);
         return;
     }
-    const Loc l = locate(x, c.inv_dx);
+    const Loc l = locate(x);
     const bool ok = valid && l.j <= (unsigned)c.ng;
     if (valid && !ok) atomicOr(err, kErrPosition);
     const unsigned W = ok ? fixed_weight(l.f) : 0u;
@@ -155,7 +155,7 @@ __device__ __forceinline__ void deposit4(const Tile &t, const float4 &xx, bool v
         bool bad = false;
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            const unsigned j = locate_ngp(xs[k], c.inv_dx);
+            const unsigned j = locate_ngp(xs[k]);
             const bool ok = valid && j - 1u <= (unsigned)c.ng;
             bad |= valid && !ok;
             if (ok && j == key) {
@@ -174,7 +174,7 @@ __device__ __forceinline__ void deposit4(const Tile &t, const float4 &xx, bool v
         bool bad = false;
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            const Loc l = locate(xs[k], c.inv_dx);
+            const Loc l = locate(xs[k]);
             const bool ok = valid && l.j <= (unsigned)c.ng;
             bad |= valid && !ok;
             const unsigned W = fixed_weight(l.f);
@@ -205,7 +205,7 @@ __device__ __forceinline__ void deposit4(const Tile &t, const float4 &xx, bool v
         bool bad = false;
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            const Loc l = locate(xs[k], c.inv_dx);
+            const Loc l = locate(xs[k]);
             const bool ok = valid && l.j <= (unsigned)c.ng;
             bad |= valid && !ok;
             const unsigned W = fixed_weight(l.f);

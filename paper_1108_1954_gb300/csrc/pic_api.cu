@@ -157,6 +157,8 @@ struct pic_run {
     cudaGraphExec_t plain = nullptr;                  // kPlainBlock steps, no sort
     PushConsts pc{};
     double dx = 0, mass = 0, q_over_dx = 0, k_rho = 0, k_e = 0, k_phi = 0;
+    double to_cells = 0, to_phys = 0;  // NG/L and L/NG (float32 positions)
+    float length32 = 0;                // (float)L: positions lie in [0, length32)
 
     template <typename T> T *at(size_t off) const { return reinterpret_cast<T *>(ws + off); }
     DevScalars *dev() const { return at<DevScalars>(lay.dev); }
@@ -269,7 +271,7 @@ cudaError_t enqueue_sort(pic_run *r, cudaStream_t s) {
         a.x = (const float *)r->xs(c); a.v = (const float *)r->vs(c);
         a.x_out = (float *)r->xs(1 - c); a.v_out = (float *)r->vs(1 - c);
         a.n = r->p.npart; a.ng = r->p.ncell;
-        a.inv_dx = r->pc.inv_dx;
+        a.inv_dx = 1.0f;                      // cell coordinates: the key is trunc(u)
         a.nchunk = r->lay.nchunk; a.chunk = r->lay.chunk;
         a.nseg = r->lay.nseg; a.seg_len = r->lay.seg_len;
         a.hist = r->at<unsigned>(r->lay.s_hist);
@@ -344,19 +346,24 @@ int read_error_word(pic_run *r) {
     return err ? PIC_EDEVICE : PIC_OK;
 }
 
-// With x, v in buffer 0: reset the run, deposit and solve: E^step ready.
-int prepare_loaded(pic_run *r, int64_t step, bool check) {
+// How the positions in buffer 0 are given.
+enum class Units { kPhysical, kCells };
+
+// With x, v in buffer 0: check (and, in the float32 modes, convert to cell
+// coordinates) the positions, reset the run, deposit and solve: E^step ready.
+int prepare_loaded(pic_run *r, int64_t step, Units units) {
     DevScalars ds{};
     ds.step = step;
     PIC_CUDA(cudaMemcpyAsync(r->dev(), &ds, sizeof(ds), cudaMemcpyHostToDevice, r->stream));
-    if (check) {
-        if (r->p.precision == PIC_FP64)
-            PIC_CUDA(launch_check_positions((const double *)r->xs(0), r->p.npart, r->p.length,
-                                            &r->dev()->err, r->sms, r->stream));
-        else
-            PIC_CUDA(launch_check_positions((const float *)r->xs(0), r->p.npart, r->pc.length,
-                                            &r->dev()->err, r->sms, r->stream));
-    }
+    if (r->p.precision == PIC_FP64)
+        PIC_CUDA(launch_check_positions((const double *)r->xs(0), r->p.npart, r->p.length,
+                                        &r->dev()->err, r->sms, r->stream));
+    else if (units == Units::kPhysical)
+        PIC_CUDA(launch_to_cells((float *)r->xs(0), r->p.npart, r->to_cells, r->pc.ngf,
+                                 r->length32, &r->dev()->err, r->sms, r->stream));
+    else
+        PIC_CUDA(launch_check_cells((const float *)r->xs(0), r->p.npart, r->pc.ngf,
+                                    &r->dev()->err, r->sms, r->stream));
     PIC_CUDA(cudaMemsetAsync(r->ws + r->lay.rho_q, 0, (size_t)r->p.ncell * 8, r->stream));
     PIC_CUDA(cudaMemsetAsync(r->ws + r->lay.rho_f32, 0, (size_t)r->p.ncell * 4, r->stream));
     PIC_CUDA(cudaMemsetAsync(r->ws + r->lay.rho_f64, 0, (size_t)r->p.ncell * 8, r->stream));
@@ -372,15 +379,15 @@ int prepare_loaded(pic_run *r, int64_t step, bool check) {
 }
 
 // Upload a state, deposit it and solve: E^step ready.
-// The positions are range-checked on the device after the upload (a host
-// loop over N positions cost more than the whole upload).
-int load_state(pic_run *r, const void *x, const void *v, int64_t step) {
+// The positions are range-checked (and converted) on the device after the
+// upload (a host loop over N positions cost more than the whole upload).
+int load_state(pic_run *r, const void *x, const void *v, int64_t step, Units units) {
     if (!x || !v) return PIC_EINVAL;
     const size_t bytes = (size_t)r->p.npart * r->elem();
     r->cur = 0;
     PIC_CUDA(cudaMemcpyAsync(r->xs(0), x, bytes, cudaMemcpyHostToDevice, r->stream));
     PIC_CUDA(cudaMemcpyAsync(r->vs(0), v, bytes, cudaMemcpyHostToDevice, r->stream));
-    return prepare_loaded(r, step, true);
+    return prepare_loaded(r, step, units);
 }
 
 }  // namespace
@@ -434,12 +441,14 @@ int pic_create(const pic_params *p, void *workspace, size_t workspace_bytes,
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&r->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) { delete r; return cuda_fail(e); }
 
-    // float32 constants of the push and the deposit's scale c = (float)(NG/L)
+    // float32 constants of the push in cell units (u = x NG/L)
     r->pc.ng = p->ncell;
-    r->pc.inv_dx = (float)((double)p->ncell / p->length);
-    r->pc.length = (float)p->length;
+    r->pc.ngf = (float)p->ncell;
+    r->pc.kdrift = (float)(p->dt * (double)p->ncell / p->length);
     r->pc.qmdt = (float)(p->qm * p->dt);
-    r->pc.dt = (float)p->dt;
+    r->to_cells = (double)p->ncell / p->length;
+    r->to_phys = p->length / (double)p->ncell;
+    r->length32 = (float)p->length;
     // float64 constants of the solve (Appendix A: Q0 = rho_init0 Lx / N, sign of qm)
     r->dx = p->length / (double)p->ncell;
     const double q0 = (p->rho_ion * p->length / (double)p->npart) * (p->qm / std::fabs(p->qm));
@@ -471,7 +480,7 @@ void pic_destroy(pic_run *run) {
 
 int pic_init(pic_run *run, const void *x0, const void *v0) {
     if (!run) return PIC_EINVAL;
-    return load_state(run, x0, v0, 0);
+    return load_state(run, x0, v0, 0, Units::kPhysical);
 }
 
 int pic_init_loaded(pic_run *run, const pic_loading *ld) {
@@ -483,12 +492,29 @@ int pic_init_loaded(pic_run *run, const pic_loading *ld) {
     if (rc) return rc;
     run->cur = 0;
     PIC_CUDA(launch_load(a, run->sms, run->stream));
-    return prepare_loaded(run, 0, false);
+    return prepare_loaded(run, 0, Units::kPhysical);
 }
 
 int pic_set_state(pic_run *run, const void *x, const void *v, int64_t step) {
     if (!run || step < 0) return PIC_EINVAL;
-    return load_state(run, x, v, step);
+    return load_state(run, x, v, step, Units::kPhysical);
+}
+
+int pic_set_cells(pic_run *run, const float *u, const void *v, int64_t step) {
+    if (!run || step < 0) return PIC_EINVAL;
+    if (run->p.precision == PIC_FP64) return PIC_EINVAL;
+    return load_state(run, u, v, step, Units::kCells);
+}
+
+int pic_get_cells(pic_run *run, float *u, void *v) {
+    if (!run) return PIC_EINVAL;
+    if (run->p.precision == PIC_FP64) return PIC_EINVAL;
+    if (!run->ready) return PIC_ESTATE;
+    const size_t bytes = (size_t)run->p.npart * run->elem();
+    if (u) PIC_CUDA(cudaMemcpyAsync(u, run->xs(run->cur), bytes, cudaMemcpyDeviceToHost, run->stream));
+    if (v) PIC_CUDA(cudaMemcpyAsync(v, run->vs(run->cur), bytes, cudaMemcpyDeviceToHost, run->stream));
+    PIC_CUDA(cudaStreamSynchronize(run->stream));
+    return read_error_word(run);
 }
 
 int pic_deposit(pic_run *run) {
@@ -592,7 +618,17 @@ int pic_get_state(pic_run *run, void *x, void *v) {
     if (!run) return PIC_EINVAL;
     if (!run->ready) return PIC_ESTATE;
     const size_t bytes = (size_t)run->p.npart * run->elem();
-    if (x) PIC_CUDA(cudaMemcpyAsync(x, run->xs(run->cur), bytes, cudaMemcpyDeviceToHost, run->stream));
+    if (x) {
+        const void *src = run->xs(run->cur);
+        if (run->p.precision != PIC_FP64) {
+            // physical positions into the idle particle buffer, then out
+            float *tmp = (float *)run->xs(1 - run->cur);
+            PIC_CUDA(launch_to_physical((const float *)src, tmp, run->p.npart, run->to_phys,
+                                        run->length32, run->sms, run->stream));
+            src = tmp;
+        }
+        PIC_CUDA(cudaMemcpyAsync(x, src, bytes, cudaMemcpyDeviceToHost, run->stream));
+    }
     if (v) PIC_CUDA(cudaMemcpyAsync(v, run->vs(run->cur), bytes, cudaMemcpyDeviceToHost, run->stream));
     PIC_CUDA(cudaStreamSynchronize(run->stream));
     return read_error_word(run);
@@ -624,7 +660,10 @@ int pic_phase_space(pic_run *run, int32_t nx, int32_t nv, double vmin, double vm
     unsigned *d = run->at<unsigned>(run->lay.phase);
     const size_t bytes = (size_t)nx * nv * 4;
     PIC_CUDA(cudaMemsetAsync(d, 0, bytes, run->stream));
-    const float sx = (float)((double)nx / run->p.length);
+    // the bin rule on the stored positions: cell coordinates in the float32
+    // modes (nx/NG), x in PIC_FP64 (nx/L)
+    const float sx = (float)((double)nx / (run->p.precision == PIC_FP64 ? run->p.length
+                                                                       : (double)run->p.ncell));
     const float sv = (float)((double)nv / (vmax - vmin));
     if (run->p.precision == PIC_FP64) {
         PhaseArgs<double> a{(const double *)run->xs(run->cur), (const double *)run->vs(run->cur),

@@ -23,18 +23,20 @@ enum : uint32_t {
     kErrInput = 8u,      // an uploaded position outside [0, L) (pic_init, pic_set_state)
 };
 
-// Float32 constants of the push, formed once on the host.
+// Float32 constants of the push, formed once on the host.  In the float32
+// modes a position is kept as its cell coordinate u = x NG / L in [0, NG)
+// (cell units: node g sits at u = g + 1/2), so the box end is the exact
+// float NG and locating a particle needs no scale factor.
 struct PushConsts {
     int ng;          // NG
-    float inv_dx;    // (float)(NG / L): the deposit's scale c
-    float length;    // (float)L
+    float ngf;       // (float)NG, exact: the box length in cell units
+    float kdrift;    // (float)(dt NG / L): u advances by v kdrift per step
     float qmdt;      // (float)(qm * dt)
-    float dt;        // (float)dt
 };
 
 // Fused push + fixed-point deposit (or deposit alone when push == false).
 struct PushArgs {
-    float *x, *v;                 // N each, 16-byte aligned
+    float *x, *v;                 // N each (x: cell coordinates), 16-byte aligned
     long long n;                  // N
     const float *E32;             // field at the nodes, float32 [NG]
     unsigned long long *rho_q;    // fixed-point density accumulator [NG]
@@ -188,6 +190,22 @@ cudaError_t launch_phase(const PhaseArgs<T> &a, int sms, cudaStream_t s);
 template <typename T>
 cudaError_t launch_check_positions(const T *x, long long n, T length, unsigned *err, int sms,
                                    cudaStream_t s);
+
+// Unit conversions of float32 positions (phase.cu), both rounded once from a
+// float64 product:
+//   to cells     u = (float)((double)x (NG/L)), a u that rounds to NG is 0;
+//                sets kErrInput unless x is in [0, (float)L); in place.
+//   to physical  x = (float)((double)u (L/NG)), at most the largest float
+//                below (float)L.
+// The host forms the same two products in pool_to_physical (ensemble.cu).
+cudaError_t launch_to_cells(float *x, long long n, double to_cells, float ngf, float length32,
+                            unsigned *err, int sms, cudaStream_t s);
+cudaError_t launch_to_physical(const float *u, float *x, long long n, double to_phys,
+                               float length32, int sms, cudaStream_t s);
+// Cell coordinates read back from a caller: every u must lie in [0, NG).
+cudaError_t launch_check_cells(const float *u, long long n, float ngf, unsigned *err, int sms,
+                               cudaStream_t s);
+float below(float v);            // the largest float below v (v > 0)
 
 // Parameter checks shared by the single-run and the pool entry points.
 int validate_params(const pic_params *p);

@@ -4,7 +4,8 @@
 // positions (Sec. 2.3).
 //
 // Design (GB300): one persistent grid of (SMs x resident blocks), each block
-// streaming float4 groups of 4 particles (x and v are separate float32 arrays,
+// streaming float4 groups of 4 particles (the cell coordinates u = x NG/L and
+// the velocities v are separate float32 arrays,
 // 16 B loads and stores, streaming cache hints: the particle arrays are read
 // and written once per step and do not fit in L2).  The block stages E in
 // shared memory and accumulates a private density tile there; the tile is
@@ -185,7 +186,7 @@ __global__ void __launch_bounds__(1024) pic_push_f32atomic_kernel(PushArgsF32Ato
     for (long long i = (long long)blockIdx.x * bs + tid; i < a.n; i += stride) {
         float x = a.x[i], v = PUSH ? a.v[i] : 0.0f;
         if (PUSH) push_particle(x, v, sE, c, ke, mom);
-        const Loc l = locate(x, c.inv_dx);
+        const Loc l = locate(x);
         if (l.j <= (unsigned)ng) {
             atomicAdd(&sRho[l.j], 1.0f - l.f);
             atomicAdd(&sRho[l.j + 1], l.f);

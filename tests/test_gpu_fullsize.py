@@ -2,8 +2,9 @@
 +-0.2 with vth 0.01, modes 1-8 at 1e-4, dt 0.1, a sort every 20 steps -- in
 the launch configuration the benchmark times: the persistent push shape the
 autotuner adopts, and pic_step_n replaying CUDA graphs of whole sort periods.
-The state comes from the device loader (same recipe as the host generator,
-counter-based) and is read back once, so oracle and GPU start identical.
+The state comes from the device loader (the recipe of the oracle's
+orc_load_two_stream, counter-based) and its cell coordinates are read back
+once, so oracle and GPU start from the same positions.
 
 * after pic_init and after the first step: the fixed-point density bit for
   bit against the oracle's fixed-point deposit of all 2^26 float32 positions,
@@ -36,8 +37,8 @@ V0, VTH = 0.2, 0.01
 LOADING = pic.Loading(v0=V0, vth=VTH, seed=2026, modes=W.two_stream_modes_1_to_8(1e-4, 2026))
 
 
-def check_density_and_field(f, x32):
-    assert np.array_equal(f["rho_q"], O.deposit_fixed(NG, L, x32))
+def check_density_and_field(f, u32):
+    assert np.array_equal(f["rho_q"], O.deposit_fixed(NG, u32))
     assert int(f["rho_q"].sum()) == N << O.FIX_BITS
     p = O.params(NG, N, L, DT)
     phi_ref, E_ref = O.field(p, O.rho_from_fixed(p, f["rho_q"]))
@@ -58,17 +59,18 @@ def tuned_run():
 
 def test_first_step_of_the_full_config_matches_the_oracle():
     run = tuned_run()
-    x0, v0 = run.get_state()
+    u0, v0 = run.get_cells()
     f0 = run.get_field()
-    check_density_and_field(f0, x0)
-    ref = O.State(O.params(NG, N, L, DT), x0, v0)
+    check_density_and_field(f0, u0)
+    # the oracle starts from the device's own positions, in float64
+    ref = O.State(O.params(NG, N, L, DT), u0.astype(np.float64) * (L / NG), v0)
     assert np.abs(f0["E"] - ref.E).max() <= fp32_field_bound(N, NG, L)
     run.step_n(1)
     x1, v1 = run.get_state()
     svv, sv = ref.step()
     assert periodic_dist(x1, ref.x, L).max() <= 1e-5 * L
     assert (np.abs(v1 - ref.v) <= 1e-5 * np.maximum(np.abs(ref.v), V0 + VTH)).all()
-    check_density_and_field(run.get_field(), x1)
+    check_density_and_field(run.get_field(), run.get_cells()[0])
     d = run.diagnostics(0, 2)
     m = ref.mass
     assert abs(d["kinetic"][0] - 0.5 * m * svv) <= 1e-5 * abs(0.5 * m * svv)
@@ -76,16 +78,16 @@ def test_first_step_of_the_full_config_matches_the_oracle():
     run.close()
 
 
-def _cells(x32):
-    c = np.float32(NG / L)
-    return np.clip((x32 * c).astype(np.float64), 0, NG - 1).astype(np.int16)
+def _cells(u32):
+    """The sort key: the cell trunc(u), clamped to the grid."""
+    return np.clip(u32.astype(np.float64), 0, NG - 1).astype(np.int16)
 
 
 def test_graph_replayed_full_config_keeps_invariants_and_sorts_stably():
     run = tuned_run()
     run.step_n(4 * S)
     assert run.step == 4 * S
-    x, v = run.get_state()
+    x, v = run.get_cells()
     check_density_and_field(run.get_field(), x)
     d = run.diagnostics(0, 4 * S + 1)
     assert (d["charge_q"] == N << O.FIX_BITS).all()
@@ -97,7 +99,7 @@ def test_graph_replayed_full_config_keeps_invariants_and_sorts_stably():
     assert np.abs(energy - energy[0]).max() <= 1e-4 * energy[0]
     # a sort of the full state: numpy's stable order by cell
     run.sort()
-    xs, vs = run.get_state()
+    xs, vs = run.get_cells()
     perm = np.argsort(_cells(x), kind="stable")
     assert np.array_equal(xs, x[perm]) and np.array_equal(vs, v[perm])
     run.close()

@@ -37,13 +37,20 @@ def test_loader_matches_the_oracle(n, modes):
 
 
 def test_init_loaded_equals_uploaded_state():
+    # the loader's physical output, uploaded, gives the same run as loading
+    # on the device: both go through the same conversion to cell units
     n, ng = 200001, 512
     ld = pic.Loading(v0=0.2, vth=0.01, seed=77, modes=((1, 1e-3, 0.0),))
     a = pic.Run(pic.Params(npart=n, ncell=ng, length=L4PI), device="cuda:0")
     a.init_loaded(ld)
-    x, v = a.get_state()
+    xd = torch.empty(n, dtype=torch.float32, device="cuda")
+    vd = torch.empty(n, dtype=torch.float32, device="cuda")
+    pic.load_two_stream(ld, n, L4PI, xd, vd)
+    torch.cuda.synchronize()
+    x, v = xd.cpu().numpy(), vd.cpu().numpy()
     b = pic.Run(pic.Params(npart=n, ncell=ng, length=L4PI), device="cuda:0")
     b.init(x, v)
+    assert np.array_equal(a.get_cells()[0], b.get_cells()[0])
     a.step_n(10)
     b.step_n(10)
     xa, va = a.get_state()

@@ -11,6 +11,7 @@ import oracle as O
 import paper_1108_1954_gb300 as pic  # noqa: E402
 import torch  # noqa: E402,F401
 import workloads as W
+from units import to_cells
 
 pytestmark = pytest.mark.gpu
 L4PI = 4.0 * math.pi
@@ -33,38 +34,41 @@ def test_ngp_density_bit_exact(n, ng):
     run = make_run(n, ng, L4PI)
     run.init(x32, v32)
     f = run.get_field()
-    assert np.array_equal(f["rho_q"], O.deposit_fixed_ngp(ng, L4PI, x32))
+    assert np.array_equal(f["rho_q"], O.deposit_fixed_ngp(ng, to_cells(x32, ng, L4PI)))
     assert int(f["rho_q"].sum()) == n << O.FIX_BITS
     run.step_n(3)
-    xs, _ = run.get_state()
-    assert np.array_equal(run.get_field()["rho_q"], O.deposit_fixed_ngp(ng, L4PI, xs))
+    us, _ = run.get_cells()
+    assert np.array_equal(run.get_field()["rho_q"], O.deposit_fixed_ngp(ng, us))
 
 
 @pytest.mark.parametrize("n,ng", [(20000, 64), (100003, 1024)])
 def test_ngp_one_step_parity(n, ng):
+    # With nearest-grid-point weighting one particle in the neighbouring cell
+    # changes E at a node by a whole particle charge, so the oracle starts
+    # from the device's own positions (its cell coordinates times dx, in
+    # float64) and every particle must then be in the same cell on both sides.
     x32, v32 = state(n, L4PI, 7 * n + ng)
     run = make_run(n, ng, L4PI)
     run.init(x32, v32)
-    ref = O.State(O.params(ng, n, L4PI, 0.1, shape=O.NGP), x32.astype(np.float64),
-                  v32.astype(np.float64))
+    u0, _ = run.get_cells()
+    dx = L4PI / ng
+    x0 = u0.astype(np.float64) * dx
+    ref = O.State(O.params(ng, n, L4PI, 0.1, shape=O.NGP), x0, v32.astype(np.float64))
+    cell_dev = np.floor(u0).astype(np.int64) % ng
+    cell_orc = (x0 / dx).astype(np.int64) % ng
+    assert np.array_equal(cell_dev, cell_orc)
+    f0 = run.get_field()
+    assert np.abs(f0["E"] - ref.E).max() <= 1e-9 * np.abs(ref.E).max()
     run.push()
     run.solve_field()
     x1, v1 = run.get_state()
     ref.step()
-    # a position within rounding of a cell boundary may fall in the other
-    # cell in float32 (floor(x c)) than in float64 (trunc(x / dx)); those
-    # few particles see the neighbouring node's field
-    c32 = np.float32(ng / L4PI)
-    cell32 = np.floor(x32 * c32).astype(np.int64) % ng
-    cell64 = np.floor(x32.astype(np.float64) / (L4PI / ng)).astype(np.int64) % ng
-    same = cell32 == cell64
-    assert same.mean() > 0.999
     d = np.abs(x1 - ref.x)
     d = np.minimum(d, L4PI - d)
-    assert d[same].max() <= 1e-5 * L4PI
+    assert d.max() <= 1e-5 * L4PI
     vscale = np.maximum(np.abs(ref.v), 0.21)
-    assert (np.abs(v1 - ref.v)[same] <= 1e-5 * vscale[same]).all()
-    assert np.array_equal(run.get_field()["rho_q"], O.deposit_fixed_ngp(ng, L4PI, x1))
+    assert (np.abs(v1 - ref.v) <= 1e-5 * vscale).all()
+    assert np.array_equal(run.get_field()["rho_q"], O.deposit_fixed_ngp(ng, run.get_cells()[0]))
 
 
 def test_ngp_momentum_conserved_and_sort_invariant():

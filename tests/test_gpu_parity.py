@@ -1,7 +1,8 @@
 """CUDA path against the FP64 oracle, through the C ABI.
 
 * the fixed-point density: bit for bit against the oracle's fixed-point
-  deposit of the GPU's own float32 positions;
+  deposit of the GPU's own float32 cell coordinates (read back with
+  get_cells; at init they are the documented conversion of the uploaded x);
 * the field: against the oracle's direct solve of the same integer density
   (1e-9 of max |E|) and of its FP64 deposit;
 * one step from identical states: positions within 1e-5 L (periodic
@@ -16,6 +17,7 @@ import pytest
 
 import oracle as O
 import workloads as W
+from units import to_cells
 
 import paper_1108_1954_gb300 as pic  # noqa: E402
 import torch  # noqa: E402,F401
@@ -46,28 +48,20 @@ def check_field_against_oracle(f, n, ng, L, dt=0.1):
 
 
 def fp32_field_bound(n, ng, L):
-    """Bound on |E_fixed - E_fp64| at the nodes for the same float32 positions.
+    """Bound on |E_fixed - E_fp64| at the nodes when the FP64 deposit takes the
+    caller's float32 positions x and the device its cell coordinates
+    u = (float)(x NG/L).
 
-    The float32 product u = x*c has a relative rounding of 2^-24, so a
-    particle's cell fraction f is off by up to u 2^-24 <= NG 2^-24 (the 2^-24
-    truncation of the fixed-point weight is smaller still).  The error moves
-    charge (NG/N) df between the particle's two nodes, so the prefix sum S_g
-    of Eq. 6 only sees the ~N/NG particles between nodes g and g+1:
-    |dS_g| ~ (NG/N) sqrt(N/NG) NG 2^-24.  E_g = (L/(2 NG)) (S_g + S_{g-1} -
-    2 mean S) then gives |dE| ~ L sqrt(NG/N) 2^-24; 16 times that covers the
-    largest of 8192 nodes with room.
-
-    A second term does not shrink with N.  The scale c itself is float32,
-    c = (float)(NG/L) = (NG/L)(1 + eta) with |eta| <= 2^-24, so the fixed-point
-    recipe sees every particle at x (1 + eta): the plasma stretched about
-    x = 0.  A sliver of the electrons' charge, |eta| L rho_ion, crosses the
-    periodic boundary (or leaves a gap before it), a point charge at the wrap
-    on a uniform background, whose field is a sawtooth of amplitude
-    |eta| L rho_ion / 2.  At NG = 4096 on L = 4 pi that is 2.53e-7, larger than
-    the first term from N ~ 2^22 on."""
-    c = ng / L
-    eta = float(np.float32(c)) / c - 1.0
-    return 16.0 * L * math.sqrt(ng / n) * 2.0 ** -24 + 0.5 * abs(eta) * L + 1e-15
+    u carries a relative rounding of 2^-24, so a particle's cell fraction f is
+    off by up to u 2^-24 <= NG 2^-24 (the 2^-24 truncation of the fixed-point
+    weight is smaller still).  The error moves charge (NG/N) df between the
+    particle's two nodes, so the prefix sum S_g of Eq. 6 only sees the ~N/NG
+    particles between nodes g and g+1: |dS_g| ~ (NG/N) sqrt(N/NG) NG 2^-24.
+    E_g = (L/(2 NG)) (S_g + S_{g-1} - 2 mean S) then gives
+    |dE| ~ L sqrt(NG/N) 2^-24; 16 times that covers the largest of 8192 nodes
+    with room.  The box is exactly [0, NG) in cell units, so no term grows
+    with the box length's float32 rounding."""
+    return 16.0 * L * math.sqrt(ng / n) * 2.0 ** -24 + 1e-15
 
 
 def one_step_parity(n, ng, L, seed, v0=0.2, vth=0.01, **kw):
@@ -76,7 +70,9 @@ def one_step_parity(n, ng, L, seed, v0=0.2, vth=0.01, **kw):
     run = make_run(n, ng, L, **kw)
     run.init(x32, v32)
     f0 = run.get_field()
-    assert np.array_equal(f0["rho_q"], O.deposit_fixed(ng, L, x32))
+    u0, _ = run.get_cells()
+    assert np.array_equal(u0, to_cells(x32, ng, L))
+    assert np.array_equal(f0["rho_q"], O.deposit_fixed(ng, u0))
     assert int(f0["rho_q"].sum()) == n << O.FIX_BITS
     check_field_against_oracle(f0, n, ng, L)
 
@@ -90,7 +86,7 @@ def one_step_parity(n, ng, L, seed, v0=0.2, vth=0.01, **kw):
     vscale = np.maximum(np.abs(ref.v), v0 + vth)
     assert (np.abs(v1 - ref.v) <= 1e-5 * vscale).all()
     f1 = run.get_field()
-    assert np.array_equal(f1["rho_q"], O.deposit_fixed(ng, L, x1))
+    assert np.array_equal(f1["rho_q"], O.deposit_fixed(ng, run.get_cells()[0]))
     check_field_against_oracle(f1, n, ng, L)
     d = run.diagnostics(0, 2)
     assert d["step"].tolist() == [0, 1]
@@ -138,7 +134,7 @@ def test_all_particles_in_one_cell():
     for variant in (1, 2, 5, 6):
         run = make_run(n, ng, L, deposit_variant=variant, block_size=256, blocks_per_sm=1)
         run.init(x32, v32)
-        assert np.array_equal(run.get_field()["rho_q"], O.deposit_fixed(ng, L, x32))
+        assert np.array_equal(run.get_field()["rho_q"], O.deposit_fixed(ng, run.get_cells()[0]))
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7])
@@ -149,7 +145,7 @@ def test_tiny_and_ragged(n):
     v32 = rng.uniform(-0.3, 0.3, n).astype(np.float32)
     run = make_run(n, ng, L)
     run.init(x32, v32)
-    assert np.array_equal(run.get_field()["rho_q"], O.deposit_fixed(ng, L, x32))
+    assert np.array_equal(run.get_field()["rho_q"], O.deposit_fixed(ng, to_cells(x32, ng, L)))
     ref = O.State(O.params(ng, n, L, 0.1), x32.astype(np.float64), v32.astype(np.float64))
     for _ in range(5):
         run.step_n(1)
@@ -157,7 +153,7 @@ def test_tiny_and_ragged(n):
         x1, v1 = run.get_state()
         assert periodic_dist(x1, ref.x, L).max() <= 1e-5 * L
         assert np.abs(v1 - ref.v).max() <= 1e-5 * 0.3
-        assert np.array_equal(run.get_field()["rho_q"], O.deposit_fixed(ng, L, x1))
+        assert np.array_equal(run.get_field()["rho_q"], O.deposit_fixed(ng, run.get_cells()[0]))
 
 
 def test_single_particle_moves_freely():

@@ -23,9 +23,10 @@ def test_phase_space_counts(nx, nv):
     run = pic.Run(pic.Params(npart=n, ncell=64, length=L4PI), device="cuda:0")
     run.init(*W.to_f32_state(x, v, L4PI))
     run.step_n(7)
-    xs, vs = run.get_state()
+    us, vs = run.get_cells()
     got = run.phase_space(nx, nv, -0.5, 0.5)
-    assert np.array_equal(got, O.phase_space(nx, nv, L4PI, -0.5, 0.5, xs, vs))
+    # the bin rule on the stored cell coordinates: a box of length NG
+    assert np.array_equal(got, O.phase_space(nx, nv, 64, -0.5, 0.5, us, vs))
     with pytest.raises(pic.PicError):
         run.phase_space(200, 200, -1.0, 1.0)           # above the bin limit
 

@@ -8,6 +8,7 @@ import pytest
 
 import oracle as O
 import workloads as W
+from units import to_cells
 
 import paper_1108_1954_gb300 as pic  # noqa: E402
 import torch  # noqa: E402,F401
@@ -83,9 +84,9 @@ def test_langmuir_frequency():
     assert abs(omega - 1.0) < 0.01
 
 
-def _keys(x, ng, L):
-    c = np.float32(ng / L)
-    return np.clip((x * c).astype(np.float64), 0, ng - 1).astype(np.int64)
+def _keys(u, ng):
+    """The sort key of a cell coordinate: trunc(u), clamped to the grid."""
+    return np.clip(u.astype(np.float64), 0, ng - 1).astype(np.int64)
 
 
 def test_sort_is_a_stable_permutation():
@@ -96,14 +97,15 @@ def test_sort_is_a_stable_permutation():
     run = make_run(n, ng, L)
     run.init(x32, v32)
     f0 = run.get_field()
+    u32 = to_cells(x32, ng, L)
     run.sort()
-    xs, vs = run.get_state()
-    k = _keys(xs, ng, L)
+    xs, vs = run.get_cells()
+    k = _keys(xs, ng)
     assert (np.diff(k) >= 0).all()
-    # same multiset of (x, v) pairs
-    a = np.lexsort((v32, x32))
+    # same multiset of (u, v) pairs
+    a = np.lexsort((v32, u32))
     b = np.lexsort((vs, xs))
-    assert np.array_equal(x32[a], xs[b]) and np.array_equal(v32[a], vs[b])
+    assert np.array_equal(u32[a], xs[b]) and np.array_equal(v32[a], vs[b])
     # stable: within a cell the original order (increasing v) is kept
     same = np.diff(k) == 0
     assert (np.diff(vs)[same] > 0).all()
@@ -123,13 +125,16 @@ def test_sorted_and_unsorted_runs_hold_the_same_particles():
     a.step_n(23)
     b.step_n(23)
     assert np.array_equal(a.get_field()["rho_q"], b.get_field()["rho_q"])
-    xa, va = a.get_state()
-    xb, vb = b.get_state()
+    xa, va = a.get_cells()
+    xb, vb = b.get_cells()
     ia, ib = np.lexsort((va, xa)), np.lexsort((vb, xb))
     assert np.array_equal(xa[ia], xb[ib]) and np.array_equal(va[ia], vb[ib])
 
 
 def test_checkpoint_restore_is_bit_identical():
+    # a checkpoint in cell coordinates (get_cells / set_cells) continues bit
+    # for bit; one in physical units (get_state / set_state) continues to the
+    # float32 rounding of the two conversions
     n, ng = 50001, 128
     x, v = W.two_stream(n, L4PI, 0.2, 0.01, 6)
     x32, v32 = W.to_f32_state(x, v, L4PI)
@@ -139,14 +144,29 @@ def test_checkpoint_restore_is_bit_identical():
     b = make_run(n, ng, L4PI, sort_interval=7)
     b.init(x32, v32)
     b.step_n(19)
-    xs, vs = b.get_state()
+    us, vs = b.get_cells()
     c = make_run(n, ng, L4PI, sort_interval=7)
-    c.set_state(xs, vs, 19)
+    c.set_cells(us, vs, 19)
     c.step_n(21)
     xa, va = a.get_state()
     xc, vc = c.get_state()
     assert np.array_equal(xa, xc) and np.array_equal(va, vc)
+    assert np.array_equal(a.get_cells()[0], c.get_cells()[0])
     assert np.array_equal(a.get_field()["rho_q"], c.get_field()["rho_q"])
+    xs, vs = b.get_state()
+    d = make_run(n, ng, L4PI, sort_interval=7)
+    d.set_state(xs, vs, 19)
+    ud, _ = d.get_cells()
+    # the round trip moves a cell coordinate by at most two float32 steps
+    # (periodically: a coordinate within a step of NG may come back as 0)
+    du = np.abs(ud.astype(np.float64) - us)
+    assert np.minimum(du, ng - du).max() <= 2.0 ** -22 * ng
+    assert d.step == 19
+    with pytest.raises(pic.PicError) as e:        # coordinates outside [0, NG)
+        bad = us.copy()
+        bad[3] = np.float32(ng)
+        d.set_cells(bad, vs, 0)
+    assert e.value.code == pic.PIC_EINVAL
 
 
 def test_graph_replay_equals_single_steps():
@@ -189,10 +209,11 @@ def test_sort_matches_stable_argsort(layout):
     v32 = (np.arange(n) * 1e-6).astype(np.float32)
     run = make_run(n, ng, L)
     run.init(x32, v32)
+    u32 = to_cells(x32, ng, L)
     run.sort()
-    xs, vs = run.get_state()
-    perm = np.argsort(_keys(x32, ng, L), kind="stable")
-    assert np.array_equal(xs, x32[perm]) and np.array_equal(vs, v32[perm])
+    xs, vs = run.get_cells()
+    perm = np.argsort(_keys(u32, ng), kind="stable")
+    assert np.array_equal(xs, u32[perm]) and np.array_equal(vs, v32[perm])
     run.sort()
-    xs2, vs2 = run.get_state()
+    xs2, vs2 = run.get_cells()
     assert np.array_equal(xs2, xs) and np.array_equal(vs2, vs)

@@ -175,6 +175,7 @@ def test_pool_run_against_the_oracle():
     step's particles within the one-step tolerances."""
     import oracle as O
     from test_gpu_parity import check_field_against_oracle, periodic_dist
+    from units import to_cells
     n, ng, L = 100003, 1024, L4PI
     modes = W.two_stream_modes_1_to_8(1e-4, 21)
     x, v = W.two_stream(n, L, 0.2, 0.01, 21, modes=modes)
@@ -187,7 +188,9 @@ def test_pool_run_against_the_oracle():
     s = pool.admit(pic.Params(npart=n, ncell=ng, length=L), x32, v32, 1)
     pool.advance(0)
     f0 = pool.get_field(s)
-    assert np.array_equal(f0["rho_q"], O.deposit_fixed(ng, L, x32))
+    u0, _ = pool.get_cells(s)
+    assert np.array_equal(u0, to_cells(x32, ng, L))
+    assert np.array_equal(f0["rho_q"], O.deposit_fixed(ng, u0))
     check_field_against_oracle(f0, n, ng, L)
     pool.advance(1)
     x1, v1 = pool.get_state(s)
@@ -197,6 +200,6 @@ def test_pool_run_against_the_oracle():
     vscale = np.maximum(np.abs(ref.v), 0.2 + 0.01)
     assert (np.abs(v1 - ref.v) <= 1e-5 * vscale).all()
     f1 = pool.get_field(s)
-    assert np.array_equal(f1["rho_q"], O.deposit_fixed(ng, L, x1))
+    assert np.array_equal(f1["rho_q"], O.deposit_fixed(ng, pool.get_cells(s)[0]))
     check_field_against_oracle(f1, n, ng, L)
     pool.close()

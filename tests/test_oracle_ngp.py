@@ -10,6 +10,7 @@ import pytest
 
 import oracle as O
 import workloads as W
+from units import to_cells
 
 L4PI = 4.0 * math.pi
 
@@ -103,19 +104,18 @@ def test_ngp_fixed_deposit_counts():
     ng, n = 64, 100003
     x, _ = W.two_stream(n, L4PI, 0.2, 0.01, 7)
     x32, _ = W.to_f32_state(x, np.zeros(n), L4PI)
-    rq = O.deposit_fixed_ngp(ng, L4PI, x32)
+    u = to_cells(x32, ng, L4PI)
+    rq = O.deposit_fixed_ngp(ng, u)
     assert rq.sum() == n << O.FIX_BITS
     assert (rq % (1 << O.FIX_BITS) == 0).all()
     # away from cell boundaries the float32 cell is the float64 cell
     x64 = x32.astype(np.float64)
     ok = _away_from_boundaries(x64, ng, L4PI, 1e-5)
     counts = np.bincount(np.floor(x64[ok] * ng / L4PI).astype(int) % ng, minlength=ng)
-    rq_ok = O.deposit_fixed_ngp(ng, L4PI, x32[ok])
+    rq_ok = O.deposit_fixed_ngp(ng, u[ok])
     assert np.array_equal(rq_ok >> O.FIX_BITS, counts)
-    # and the float32 recipe itself on hand-picked values: u = x * c, floor
-    c = np.float32(ng / L4PI)
-    for xv in (np.float32(0.0), np.nextafter(np.float32(L4PI), np.float32(0.0)),
-               np.float32(L4PI / ng), np.float32(1.0)):
-        want = int(np.floor(np.float32(xv) * c)) % ng
-        got = np.nonzero(O.deposit_fixed_ngp(ng, L4PI, np.array([xv], dtype=np.float32)))[0]
+    # and the recipe itself on hand-picked coordinates: the cell is floor(u)
+    for uv in (0.0, np.nextafter(np.float32(ng), np.float32(0.0)), 1.0, 0.99999994, 17.5):
+        want = int(np.floor(np.float32(uv))) % ng
+        got = np.nonzero(O.deposit_fixed_ngp(ng, np.array([uv], dtype=np.float32)))[0]
         assert list(got) == [want]

@@ -14,6 +14,7 @@ import pytest
 
 import oracle as O
 import workloads as W
+from units import to_cells
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 L4PI = 4.0 * math.pi
@@ -326,54 +327,56 @@ def test_fixed_deposit_golden_cases():
     rows = [l.split() for l in open(os.path.join(GOLDEN, "fixed_deposit_dyadic.txt"))
             if l.strip() and not l.startswith("#")]
     for r in rows:
-        x = np.array([float(r[0])], dtype=np.float32)
+        u = np.array([float(r[0])], dtype=np.float32)
         want = np.array([int(t) for t in r[1:]], dtype=np.int64)
-        np.testing.assert_array_equal(O.deposit_fixed(4, 4.0, x), want)
+        np.testing.assert_array_equal(O.deposit_fixed(4, u), want)
 
 
 def test_fixed_deposit_exact_total_and_fp64_agreement():
     n, ng, lx = 20000, 64, L4PI
     x, v = W.two_stream(n, lx, 0.2, 0.01, 4)
     x32, _ = W.to_f32_state(x, v, lx)
-    rq = O.deposit_fixed(ng, lx, x32)
+    u = to_cells(x32, ng, lx)
+    rq = O.deposit_fixed(ng, u)
     assert int(rq.sum()) == n * (1 << O.FIX_BITS)
     assert rq.min() >= 0
     p = O.params(ng, n, lx)
     rho_fix = O.rho_from_fixed(p, rq)
-    rho64 = O.deposit(p, x32.astype(np.float64))
-    # per particle the float32 fraction differs from the FP64 weight by at
-    # most a few units of 2^-24 * NG, so rho differs by <~ (NG/N) * count * that
-    assert np.abs(rho_fix - rho64).max() < 1e-5
+    rho64 = O.deposit(p, u.astype(np.float64) * (lx / ng))
+    # the only difference from the FP64 weighting of the same positions is the
+    # truncation of each weight to 2^-24 of a particle: a node's density
+    # differs by at most (NG/N) * (particles at the node) * 2^-24
+    assert np.abs(rho_fix - rho64).max() < 4 * 2.0 ** -24
     assert abs(rho_fix.sum()) < 1e-10
 
 
 def _lattice_fields(n, ng, lx):
     x, v = W.lattice_positions(n, lx), np.zeros(n)
     x32, _ = W.to_f32_state(x, v, lx)
+    u = to_cells(x32, ng, lx)
     p = O.params(ng, n, lx)
-    E_fix = O.field(p, O.rho_from_fixed(p, O.deposit_fixed(ng, lx, x32)))[1]
-    E_64 = O.field(p, O.deposit(p, x32.astype(np.float64)))[1]
+    E_fix = O.field(p, O.rho_from_fixed(p, O.deposit_fixed(ng, u)))[1]
+    E_64 = O.field(p, O.deposit(p, u.astype(np.float64) * (lx / ng)))[1]
     return E_fix, E_64
 
 
-def test_fixed_deposit_float32_scale_ramp():
-    # The recipe's scale c = (float)(NG/L) = (NG/L)(1 + eta) places every
-    # particle at x (1 + eta): the plasma stretched by 1 + eta, a charge
-    # |eta| L rho_ion carried across the wrap.  On a uniform lattice, whose
-    # FP64 field is zero, the fixed-point field is the ramp that charge
-    # makes: dE/dx = eta rho_ion between the wrap's two ends (E rises by
-    # eta L over the box), amplitude |eta| L / 2.
-    n, ng, lx = 1 << 22, 1024, L4PI
+@pytest.mark.parametrize("n,ng,lx", [(1 << 22, 1024, L4PI), (1 << 20, 4096, L4PI),
+                                     (20000, 64, L4PI), (1 << 20, 100, 10.0)])
+def test_fixed_deposit_has_no_box_scale_ramp(n, ng, lx):
+    # In cell coordinates the box is exactly [0, NG): the uniform lattice has
+    # no field beyond the float32 rounding of its positions.  A recipe that
+    # scaled physical float32 positions by c = (float)(NG/L) = (NG/L)(1 + eta)
+    # would stretch the plasma by 1 + eta and carry a charge |eta| L across
+    # the wrap: a sawtooth field of slope eta and amplitude |eta| L / 2
+    # (2.5e-7 at NG = 1024 on L = 4 pi).  The fixed-point field must equal the
+    # FP64 weighting of the same positions to the 2^-24 truncation level and
+    # stay far below that sawtooth.
+    E_fix, E_64 = _lattice_fields(n, ng, lx)
+    assert np.abs(E_fix - E_64).max() <= 1e-10
+    assert np.abs(E_fix).max() <= 1e-7 * lx / (4 * math.pi)
     c = ng / lx
     eta = float(np.float32(c)) / c - 1.0
-    amp = 0.5 * abs(eta) * lx
-    assert amp > 2e-7
-    E_fix, E_64 = _lattice_fields(n, ng, lx)
-    assert np.abs(E_64).max() < 0.02 * amp
-    g = np.arange(1, ng - 1)
-    slope = np.polyfit(g, E_fix[1:-1], 1)[0]
-    assert abs(slope * ng / (eta * lx) - 1.0) < 0.05
-    assert abs(np.abs(E_fix).max() / amp - 1.0) < 0.1
-    # a box whose scale is exact in float32 (c = 10) has no ramp
-    E_fix, _ = _lattice_fields(1 << 20, 100, 10.0)
-    assert np.abs(E_fix).max() < 1e-3 * 0.5 * 2.0 ** -24 * 10.0
+    if eta != 0.0:
+        g = np.arange(1, ng - 1)
+        slope = np.polyfit(g, E_fix[1:-1], 1)[0] * ng / lx
+        assert abs(slope) < 0.01 * abs(eta)

@@ -4,10 +4,10 @@ reservation, code that cannot pay for cudaMalloc's synchronisation).  Its
 scratch lives in a device array inside the library, shared by every call.
 
 The test calls the entry point through the C ABI on caller-owned device
-buffers, twice in a row with different inputs, and compares each result with
-pic_sort of a run holding the same particles and with numpy's stable argsort
-of the cell keys.  A stable sort by cell has one answer, so all three must
-agree bit for bit.  Bad pointers (misaligned, overlapping) are refused on the
+buffers, several times in a row with different inputs, and compares each
+result with pic_sort of a run holding the same particles and with numpy's
+stable argsort of the cell keys.  A stable sort by cell has one answer, so
+all three must agree bit for bit.  Bad pointers (misaligned, overlapping) are refused on the
 host before anything is launched.  This file is collected last."""
 import ctypes as C
 import math
@@ -31,12 +31,15 @@ def _entry():
 
 
 def _sorted_by_pic_sort(x, v, ncell):
+    """A run holding the particles, sorted by pic_sort: its cell coordinates
+    u = x NG/L before and after the sort."""
     run = pic.Run(pic.Params(npart=x.size, ncell=ncell, length=L), device="cuda:0")
     run.init(x, v)
+    u, _ = run.get_cells()
     run.sort()
-    xs, vs = run.get_state()
+    us, vs = run.get_cells()
     run.close()
-    return xs, vs
+    return u, us, vs
 
 
 def _stable_argsort_by_cell(x, ncell, length):
@@ -50,6 +53,10 @@ def _stable_argsort_by_cell(x, ncell, length):
 
 
 def test_noalloc_sort_matches_pic_sort_and_argsort_twice():
+    # A run keeps its positions as cell coordinates u in [0, NG), so the
+    # entry point sorts those with L = NG (the cell of u is trunc(u)), the
+    # key pic_sort uses; a second call sorts physical positions, compared
+    # with numpy alone.
     fn = _entry()
     stream = torch.cuda.current_stream()
     for call, (n, ncell) in enumerate([(300001, 1024), (2_000_003, 4096)]):
@@ -57,21 +64,23 @@ def test_noalloc_sort_matches_pic_sort_and_argsort_twice():
         x = rng.uniform(0, L, n).astype(np.float32)
         x[x >= np.float32(L)] = 0.0
         v = rng.standard_normal(n).astype(np.float32)
-        xd = torch.from_numpy(x).to("cuda")
-        vd = torch.from_numpy(v).to("cuda")
-        xo = torch.empty_like(xd)
-        vo = torch.empty_like(vd)
-        rc = fn(xd.data_ptr(), vd.data_ptr(), xo.data_ptr(), vo.data_ptr(), n, ncell, L,
-                stream.cuda_stream)
-        assert rc == pic.PIC_OK
-        torch.cuda.synchronize()
-        xr, vr = _sorted_by_pic_sort(x, v, ncell)
-        got_x, got_v = xo.cpu().numpy(), vo.cpu().numpy()
-        assert np.array_equal(got_x, xr)
-        assert np.array_equal(got_v, vr)
-        order = _stable_argsort_by_cell(x, ncell, L)
-        assert np.array_equal(got_x, x[order])
-        assert np.array_equal(got_v, v[order])
+        u, ur, vr = _sorted_by_pic_sort(x, v, ncell)
+        for pos, length in ((u, float(ncell)), (x, L)):
+            xd = torch.from_numpy(pos).to("cuda")
+            vd = torch.from_numpy(v).to("cuda")
+            xo = torch.empty_like(xd)
+            vo = torch.empty_like(vd)
+            rc = fn(xd.data_ptr(), vd.data_ptr(), xo.data_ptr(), vo.data_ptr(), n, ncell,
+                    length, stream.cuda_stream)
+            assert rc == pic.PIC_OK
+            torch.cuda.synchronize()
+            got_x, got_v = xo.cpu().numpy(), vo.cpu().numpy()
+            if pos is u:
+                assert np.array_equal(got_x, ur)
+                assert np.array_equal(got_v, vr)
+            order = _stable_argsort_by_cell(pos, ncell, length)
+            assert np.array_equal(got_x, pos[order])
+            assert np.array_equal(got_v, v[order])
 
 
 def test_noalloc_sort_rejects_sizes_beyond_its_limits():
