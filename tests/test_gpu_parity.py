@@ -137,6 +137,29 @@ def test_all_particles_in_one_cell():
         assert np.array_equal(run.get_field()["rho_q"], O.deposit_fixed(ng, run.get_cells()[0]))
 
 
+@pytest.mark.parametrize("variant,block,unroll", [(1, 512, 1), (5, 64, 4), (2, 256, 2)])
+def test_one_node_of_a_tile_wraps_many_times(variant, block, unroll):
+    # 2^24 particles at one position, one block per SM: a block adds ~110,000
+    # weights of about 2^24 to each of two nodes of its tile, so each node's
+    # low word wraps thousands of times and every carry must reach the high
+    # word.  The exact sums are N (2^24 - W) and N W.
+    n, ng = 1 << 24, 64
+    u = np.float32(10.3)
+    x32 = np.full(n, u * np.float32(2.0 / ng), dtype=np.float32)   # L = 2: x = u dx
+    v32 = np.zeros(n, dtype=np.float32)
+    run = make_run(n, ng, 2.0, deposit_variant=variant, block_size=block, unroll=unroll,
+                   blocks_per_sm=1)
+    run.init(x32, v32)
+    uc, _ = run.get_cells()
+    want = O.deposit_fixed(ng, uc)
+    assert np.count_nonzero(want) == 2 and np.unique(uc).size == 1
+    assert np.array_equal(run.get_field()["rho_q"], want)
+    run.deposit()
+    run.solve_field()
+    assert np.array_equal(run.get_field()["rho_q"], want)
+    run.close()
+
+
 @pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7])
 def test_tiny_and_ragged(n):
     ng, L = 16, 3.0
