@@ -350,21 +350,35 @@ def ensemble_states(nrun, seed):
 
 
 def tune_pool(states, steps, history):
-    """Autotuner of the batched launch: the whole ensemble is admitted once;
-    each (variant, cluster, block) is then timed over `steps` steps (after
-    `steps` untimed ones) on the same resident runs, the shape changed with
-    pic_pool_configure.  Returns the fastest and the table."""
+    """Autotuner of the batched launch, over the deposit variant and build,
+    the cluster size, the block size (the tile shape) and the sort interval.
+    The whole ensemble is admitted once; each (variant, cluster, block) is
+    timed over `steps` steps (after `steps` untimed ones) on the same
+    resident runs, the shape changed with pic_pool_configure.  Then, with the
+    fastest shape, the ensemble is admitted again for each sort interval S
+    and timed over 40 steps (after 10), long enough to include the sorts of
+    every S tried.  Returns the fastest (variant, cluster, block, S) and the
+    two tables."""
     import torch
     import paper_1108_1954_gb300 as pic
-    nbytes = sum(pic.pool_run_bytes(p, history) for p, _, _ in states) + (64 << 20)
-    pool = pic.Pool(max_slots=len(states), ncell_max=2048, arena_bytes=nbytes,
-                    history=history, variant=5, cluster=8, block=512)
-    for p, x, v in states:
-        pool.admit(p, x, v, 1 << 40)
-    pool.advance(0)
-    pool.sync()
-    table = []
     e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+
+    def admit_all(S):
+        nbytes = sum(pic.pool_run_bytes(pic.Params(npart=p.npart, ncell=p.ncell, length=p.length,
+                                                   sort_interval=S), history)
+                     for p, _, _ in states) + (64 << 20)
+        pool = pic.Pool(max_slots=len(states), ncell_max=2048, arena_bytes=nbytes,
+                        history=history, variant=5, cluster=8, block=512)
+        for p, x, v in states:
+            q = pic.Params(npart=p.npart, ncell=p.ncell, length=p.length, dt=p.dt,
+                           sort_interval=S)
+            pool.admit(q, x, v, 1 << 40)
+        pool.advance(0)
+        pool.sync()
+        return pool
+
+    pool = admit_all(0)
+    table = []
     for variant in (1, 2, 5, 6, 1 + 16, 2 + 16, 5 + 16, 6 + 16):
         for cluster in (4, 8):
             for block in (256, 512):
@@ -380,7 +394,20 @@ def tune_pool(states, steps, history):
                 table.append(((variant, cluster, block), e0.elapsed_time(e1)))
     pool.close()
     table.sort(key=lambda t: t[1])
-    return table[0][0], table
+    shape = table[0][0]
+    sort_table = []
+    for S in (0, 10, 20, 40):
+        pool = admit_all(S)
+        pool.configure(*shape)
+        pool.advance(10)
+        e0.record(pool.stream)
+        pool.advance(40)
+        e1.record(pool.stream)
+        pool.sync()
+        pool.close()
+        sort_table.append((S, e0.elapsed_time(e1) / 40.0))
+    sort_table.sort(key=lambda t: t[1])
+    return shape + (sort_table[0][0],), table, sort_table
 
 
 def time_batched(args):
@@ -392,13 +419,16 @@ def time_batched(args):
     states = ensemble_states(args.batched_runs, 3)
     total_particles = sum(p.npart for p, _, _ in states)
     if args.no_tune_batched:
-        best, table = (1 + 16, 8, 256), []
+        best, table, sort_table = (1 + 16, 8, 256, 0), [], []
     else:
-        best, table = tune_pool(states, 10, H)
-    nbytes = sum(pic.pool_run_bytes(p, H) for p, _, _ in states) + (64 << 20)
+        best, table, sort_table = tune_pool(states, 10, H)
+    S = best[3]
+    sorted_states = [(pic.Params(npart=p.npart, ncell=p.ncell, length=p.length, dt=p.dt,
+                                 sort_interval=S), x, v) for p, x, v in states]
+    nbytes = sum(pic.pool_run_bytes(p, H) for p, _, _ in sorted_states) + (64 << 20)
     pool = pic.Pool(max_slots=len(states), ncell_max=2048, arena_bytes=nbytes, history=H,
                     variant=best[0], cluster=best[1], block=best[2])
-    for p, x, v in states:
+    for p, x, v in sorted_states:
         pool.admit(p, x, v, K)
     pool.advance(0)
     pool.sync()
@@ -410,13 +440,14 @@ def time_batched(args):
     t_batched = e0.elapsed_time(e1) / 1e3
     pool.close()
     del pool
-    # one run per launch sequence: every run through its own pic_step_n
+    # one run per launch sequence: every run through its own pic_step_n,
+    # with the same sort interval
     runs = []
-    for p, x, v in states:
+    for p, x, v in sorted_states:
         r = pic.Run(pic.Params(npart=p.npart, ncell=p.ncell, length=p.length, dt=p.dt,
-                               history=max(64, K + 1)))
+                               sort_interval=S, history=max(64, K + 1)))
         r.init(x, v)
-        r.step_n(16)            # capture its graph outside the timed region
+        r.step_n(3 * S if S else 16)    # capture its graphs outside the timed region
         runs.append(r)
     torch.cuda.synchronize()
     s = torch.cuda.current_stream()
@@ -433,8 +464,10 @@ def time_batched(args):
             "value": total_particles * K / t_batched, "unit": "particle-steps/s",
             "seconds": t_batched, "plain_value": total_particles * K / t_plain,
             "plain_seconds": t_plain, "speedup_vs_plain": t_plain / t_batched,
-            "launch": {"variant": best[0], "cluster": best[1], "block": best[2]},
-            "tune": [[list(c), round(ms, 3)] for c, ms in table[:6]]}
+            "launch": {"variant": best[0], "cluster": best[1], "block": best[2],
+                       "sort_interval": S},
+            "tune": [[list(c), round(ms, 3)] for c, ms in table[:6]],
+            "tune_sort_interval": [[S_, round(ms, 4)] for S_, ms in sort_table]}
 
 
 def precision_study(args):
@@ -753,7 +786,8 @@ def compact_batched(b):
     return {"runs": b["runs"], "steps": b["steps"], "particles": b["particles"],
             "value": sig(b["value"]), "plain_value": sig(b["plain_value"]),
             "speedup_vs_plain": sig(b["speedup_vs_plain"], 3), "unit": b["unit"],
-            "launch": b["launch"], "tune_top": b["tune"][:3]}
+            "launch": b["launch"], "tune_top": b["tune"][:3],
+            "tune_sort_interval_ms_per_step": b["tune_sort_interval"]}
 
 
 def compact_served(sv):

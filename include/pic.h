@@ -357,6 +357,10 @@ int pic_autotune(pic_run *run, int32_t reps, pic_tune_entry *results,
  * pic_pool_advance, which launches one thread-block-cluster kernel for all
  * runs with steps left: each cluster takes runs from a queue, largest work
  * first, and keeps a run on chip through all of its steps of that launch.
+ * A run with sort_interval S > 0 sorts its particles by cell before every
+ * step n > 0 with n % S == 0, as the single run does (a stable counting sort
+ * inside the cluster, into a second pair of particle buffers: 8 N more
+ * arena bytes).
  * ------------------------------------------------------------------------ */
 
 typedef struct pic_pool pic_pool;
@@ -374,8 +378,9 @@ typedef struct pic_pool_config {
 } pic_pool_config;
 
 /* Arena bytes one run with parameters *p takes in a pool with `history`
- * rows.  PIC_EINVAL for what no pool admits: a precision other than
- * PIC_FP32_FIXED, the CG solver, the NGP shape, history < 1. */
+ * rows (twice the particle bytes when it sorts).  PIC_EINVAL for what no
+ * pool admits: a precision other than PIC_FP32_FIXED, the CG solver, the
+ * NGP shape, history < 1. */
 int pic_pool_run_bytes(const pic_params *p, int32_t history, size_t *bytes);
 
 /* Bytes at the start of the arena for the pool's own tables. */

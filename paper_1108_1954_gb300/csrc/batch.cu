@@ -21,6 +21,10 @@
 //   C  each block copies the other slices of E into its own shared copy;
 //      block 0 sums the slice diagnostics over the blocks and writes the
 //      step's history rows just before the next step's first barrier.
+// A run with a sort interval S > 0 first sorts its particles by cell before
+// every step n > 0 with n % S == 0 (the steps at which the single run sorts):
+// a stable counting sort inside the cluster (cluster_sort below), from the
+// run's buffers into its second pair, which then holds the state.
 //
 // A slice has at most one node per thread (ceil(NG/C) <= block, checked by
 // the pool), so the integer solve of a slice is one block-wide scan.
@@ -50,8 +54,138 @@ struct Exchange {
     double kv[2];                 // push sums (v_old v_new, v_new)
     double diag[kDiagFields];     // slice diagnostics
     unsigned long long cq;        // slice sum of rho_q
+    unsigned sort_total;          // the sort: particles in the block's cell slice
     int ticket;                   // block 0: the run being processed
 };
+
+// Extra words of each tile array beyond NG + 2: the sort keeps a table of
+// C x ceil(NG/C) <= NG + C - 1 words in one of them.
+constexpr int kTilePad = kMaxCluster + 8;
+
+// The sort key of a cell coordinate: trunc(u) clamped to [0, NG-1] (NaN to
+// 0), the key of the single run's counting sort (sort.cu).
+__device__ __forceinline__ unsigned sort_key(float u, int ng) {
+    u = u > 0.0f ? u : 0.0f;
+    const float top = (float)(ng - 1);
+    u = u < top ? u : top;
+    return (unsigned)u;
+}
+
+// Stable counting sort of one run's particles by cell, in one cluster.
+// Block r owns the contiguous particle chunk [c0, c1) (the chunks in rank
+// order cover the run) and the cell slice [b0, b1) of at most one cell per
+// thread.  Four cluster barriers:
+//   count    each block counts the cells of its chunk into tile.lo;
+//   #1       the owner of cell g reads the C blocks' counts of g and forms
+//            the per-block exclusive prefixes and the cell total; a block
+//            scan over its slice gives the slice-local bases and the slice
+//            total, published in ex.sort_total;
+//   #2       every owner adds the totals of the slices before its own and
+//            writes its table T[r'][g - b0] = first slot of block r' in cell
+//            g into tile.hi;
+//   #3       every block reads its first slot of every cell from the owners'
+//            tables into tile.lo and scatters its chunk in order, 256
+//            particles at a time (lanes of one cell ranked by match, warps
+//            taking their slots one after the other), into xa, va;
+//   #4       the scattered particles are visible to the whole cluster.
+// The order within a cell is the input order, so the result is the unique
+// stable order by cell: the single run's sort, bit for bit.
+__device__ void cluster_sort(const BatchArgs &a, cg::cluster_group &cl, Exchange &ex,
+                             const Tile &tile, const float *X, const float *V, float *XA,
+                             float *VA, long long n, int ng, long long c0, long long c1,
+                             int b0, int b1, int P) {
+    __shared__ unsigned wsum[32];
+    const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
+    const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const int nwarp = bs >> 5;
+    // count (the tile is empty at the start of a step)
+    for (long long i = c0 + tid; i < c1; i += bs) atomicAdd(&tile.lo[sort_key(X[i], ng)], 1u);
+    cl.sync();                                                        // #1
+    const int g = b0 + tid;
+    const bool mine = g < b1;
+    unsigned cnt[kMaxCluster];
+#pragma unroll
+    for (int b = 0; b < kMaxCluster; b++)
+        cnt[b] = (mine && b < C) ? cl.map_shared_rank(tile.lo, b)[g] : 0u;
+    unsigned tot = 0;
+#pragma unroll
+    for (int b = 0; b < kMaxCluster; b++) tot += cnt[b];
+    // block-wide exclusive scan of the cell totals over the slice
+    unsigned inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned u = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += u;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    unsigned woff = 0, stot = 0;
+    for (int w = 0; w < nwarp; w++) {
+        if (w < warp) woff += wsum[w];
+        stot += wsum[w];
+    }
+    const unsigned local = woff + inc - tot;          // slots before g within the slice
+    if (tid == 0) ex.sort_total = stot;
+    cl.sync();                                                        // #2
+    unsigned before = 0;                               // particles in slices < r
+    if (tid < 32) {
+        unsigned t = (tid < r) ? cl.map_shared_rank(&ex.sort_total, tid)[0] : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(kFull, t, o);
+        if (tid == 0) wsum[0] = t;
+    }
+    __syncthreads();
+    before = wsum[0];
+    if (mine) {
+        unsigned slot = before + local;
+#pragma unroll
+        for (int b = 0; b < kMaxCluster; b++) {
+            if (b < C) tile.hi[b * P + tid] = slot;
+            slot += cnt[b];
+        }
+    }
+    cl.sync();                                                        // #3
+    // this block's first slot of every cell, from the cell's owner
+    for (int h = tid; h < ng; h += bs) {
+        const int o = h / P;
+        tile.lo[h] = cl.map_shared_rank(tile.hi, o)[r * P + (h - o * P)];
+    }
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    for (long long i0 = c0; i0 < c1; i0 += bs) {
+        const long long i = i0 + tid;
+        const bool valid = i < c1;
+        const float x = valid ? X[i] : 0.0f, v = valid ? V[i] : 0.0f;
+        const unsigned key = valid ? sort_key(x, ng) : 0xffffffffu;
+        const unsigned peers = __match_any_sync(kFull, key);
+        const int leader = __ffs(peers) - 1;
+        unsigned base = 0;
+        for (int w = 0; w < nwarp; w++) {
+            if (w == warp && valid && lane == leader) {
+                base = tile.lo[key];
+                tile.lo[key] = base + (unsigned)__popc(peers);
+            }
+            __syncthreads();
+        }
+        base = __shfl_sync(kFull, base, leader);
+        if (valid) {
+            const unsigned long long dst = (unsigned long long)base + __popc(peers & lt);
+            if (dst < (unsigned long long)n) {
+                XA[dst] = x;
+                VA[dst] = v;
+            } else {
+                atomicOr(a.err, kErrSortKey);
+            }
+        }
+    }
+    cl.sync();                                                        // #4
+    // the tile empty again for the push (hi held the table: C P words)
+    for (int j = tid; j < ng + kTilePad; j += bs) {
+        tile.lo[j] = 0u;
+        tile.hi[j] = 0u;
+    }
+    __syncthreads();
+}
 
 template <int VARIANT>
 __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_group &cl,
@@ -80,8 +214,8 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
     const int b0 = min(ng, r * P), b1 = min(ng, b0 + P);
     const long long n4 = R.n >> 2;
     const long long qlo = n4 * r / C, qhi = n4 * (r + 1) / C;
-    float4 *x4 = reinterpret_cast<float4 *>(R.x);
-    float4 *v4 = reinterpret_cast<float4 *>(R.v);
+    // the state's buffers and the sort's destination; they swap after a sort
+    float *X = R.x, *V = R.v, *XA = R.xa, *VA = R.va;
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
 
     // Block 0: the history rows of step s from the blocks' slice
@@ -121,6 +255,18 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
 
     for (int s = 0; s < steps; s++) {
         const bool last = s == steps - 1;
+        const long long nabs = step0 + s;
+        if (push && R.sort_interval > 0 && nabs > 0 && nabs % R.sort_interval == 0) {
+            // the sort touches only the tiles and ex.sort_total: the slice
+            // diagnostics of step s-1 that block 0 reads below stay as they
+            // are until this step's barrier #2
+            cluster_sort(a, cl, ex, tile, X, V, XA, VA, R.n, ng, 4 * qlo,
+                         r == C - 1 ? R.n : 4 * qhi, b0, b1, P);
+            float *t = X; X = XA; XA = t;
+            t = V; V = VA; VA = t;
+        }
+        float4 *x4 = reinterpret_cast<float4 *>(X);
+        float4 *v4 = reinterpret_cast<float4 *>(V);
         // ---- A: push + deposit into the own tile; kU float4 groups per
         // thread per iteration, the next iteration's loads issued first
         float ke = 0.0f, mom = 0.0f;
@@ -165,10 +311,10 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
         if (r == 0 && tid < 32) {                 // the last N mod 4 particles
             const long long i = n4 * 4 + lane;
             const bool valid = i < R.n;
-            float xs = valid ? R.x[i] : 0.0f, vs = valid && push ? R.v[i] : 0.0f;
+            float xs = valid ? X[i] : 0.0f, vs = valid && push ? V[i] : 0.0f;
             if (push && valid) push_particle(xs, vs, sE, c, ke, mom);
             deposit_one<VARIANT>(tile, xs, valid, c, a.err, lane);
-            if (push && valid) { R.x[i] = xs; R.v[i] = vs; }
+            if (push && valid) { X[i] = xs; V[i] = vs; }
         }
         if (r == 0 && s > 0) write_rows(s - 1);     // the previous step's rows
         cl.sync();                                                    // #1
@@ -361,8 +507,8 @@ __global__ void __launch_bounds__(512, MINB) pic_batch_kernel(BatchArgs a) {
     const int ngm = a.ng_max;
     Tile tile;
     tile.lo = reinterpret_cast<unsigned *>(smem_raw);
-    tile.hi = tile.lo + ngm + 2;
-    float *sE = reinterpret_cast<float *>(tile.hi + ngm + 2);
+    tile.hi = tile.lo + ngm + kTilePad;
+    float *sE = reinterpret_cast<float *>(tile.hi + ngm + kTilePad);
     for (;;) {
         if (cl.block_rank() == 0 && threadIdx.x == 0) ex.ticket = (int)atomicAdd(a.next, 1u);
         cl.sync();
@@ -402,7 +548,7 @@ BatchKernel pick_batch(int code) {
 size_t batch_smem_bytes(int ng_max, int cluster, int block) {
     (void)cluster;
     (void)block;
-    return (size_t)(ng_max + 2) * 12;
+    return (size_t)(ng_max + kTilePad) * 8 + (size_t)(ng_max + 2) * 4;
 }
 
 cudaError_t batch_prepare_attributes() {

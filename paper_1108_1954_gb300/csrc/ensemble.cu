@@ -5,8 +5,9 @@
 //
 // Arena layout: [descriptor table | order table | ticket + error word] then
 // the runs, each a 256-byte-aligned block from a first-fit free list:
-//   x[N], v[N] (float32), E32[NG], E64[NG], phi[NG], rho[NG], rho_q_last[NG],
-//   history[H], step counter.
+//   x[N], v[N] (float32), [x'[N], v'[N]: the sort's destination, when the run
+//   sorts], E32[NG], E64[NG], phi[NG], rho[NG], rho_q_last[NG], history[H],
+//   step counter.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -26,7 +27,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct RunLayout {
-    size_t x, v, E32, E64, phi, rho, rq, hist, step, total;
+    size_t x, v, xa, va, E32, E64, phi, rho, rq, hist, step, total;
 };
 
 RunLayout run_layout(const pic_params *p, int history) {
@@ -36,6 +37,8 @@ RunLayout run_layout(const pic_params *p, int history) {
     auto take = [&](size_t b) { size_t o = off; off = align_up(off + b); return o; };
     L.x = take(4 * n);
     L.v = take(4 * n);
+    L.xa = p->sort_interval > 0 ? take(4 * n) : 0;
+    L.va = p->sort_interval > 0 ? take(4 * n) : 0;
     L.E32 = take(4 * ng);
     L.E64 = take(8 * ng);
     L.phi = take(8 * ng);
@@ -112,6 +115,19 @@ struct pic_pool {
         RunLayout lay{};
         BatchRun desc{};
         int64_t target = 0, done = 0;
+        float *buf_x[2] = {nullptr, nullptr}, *buf_v[2] = {nullptr, nullptr};
+
+        // The buffers holding the state after `done` steps: a sort precedes
+        // every step n > 0 with n % S == 0, so floor((done - 1) / S) sorts
+        // have run; each swaps the pair.
+        void point_at_state() {
+            const int S = p.sort_interval;
+            const int cur = (S > 0 && done >= 1) ? (int)(((done - 1) / S) & 1) : 0;
+            desc.x = buf_x[cur];
+            desc.v = buf_v[cur];
+            desc.xa = buf_x[1 - cur];
+            desc.va = buf_v[1 - cur];
+        }
     };
     std::vector<Slot> slots;
     std::vector<BatchRun> h_runs;
@@ -300,8 +316,12 @@ int admit_common(pic_pool *pool, const pic_params *p, int64_t steps, int32_t *sl
     sl.done = 0;
     unsigned char *base = pool->arena + off;
     BatchRun &d = sl.desc;
-    d.x = (float *)(base + L.x);
-    d.v = (float *)(base + L.v);
+    sl.buf_x[0] = (float *)(base + L.x);
+    sl.buf_v[0] = (float *)(base + L.v);
+    sl.buf_x[1] = p->sort_interval > 0 ? (float *)(base + L.xa) : nullptr;
+    sl.buf_v[1] = p->sort_interval > 0 ? (float *)(base + L.va) : nullptr;
+    sl.point_at_state();
+    d.sort_interval = p->sort_interval;
     d.n = p->npart;
     d.pc.ng = p->ncell;
     d.pc.ngf = (float)p->ncell;
@@ -436,7 +456,10 @@ int pic_pool_advance(pic_pool *pool, int64_t k, int32_t *active) {
     });
     int rc = launch(pool, order, true);
     if (rc) return rc;
-    for (int i : order) pool->slots[i].done += pool->slots[i].desc.steps;
+    for (int i : order) {
+        pool->slots[i].done += pool->slots[i].desc.steps;
+        pool->slots[i].point_at_state();
+    }
     if (active) *active = (int32_t)order.size();
     return PIC_OK;
 }

@@ -127,7 +127,9 @@ struct SortArgs {
 
 // One run of a batched ensemble (device descriptor; host-built).
 struct BatchRun {
-    float *x, *v;                 // particles, 16-byte aligned
+    float *x, *v;                 // particles (cell coordinates u), 16-byte aligned
+    float *xa, *va;               // the sort's destination (sort_interval > 0)
+    int sort_interval;            // S: sort by cell before steps n % S == 0, n > 0
     long long n;                  // N
     PushConsts pc;                // ng, c = NG/L, L, qm dt, dt (float32)
     float *E32;                   // [NG] field of the current step (state)

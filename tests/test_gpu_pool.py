@@ -35,7 +35,7 @@ def run_set():
 
 def alone(p, x32, v32, steps):
     run = pic.Run(pic.Params(npart=p.npart, ncell=p.ncell, length=p.length, dt=p.dt,
-                             history=512), device="cuda:0")
+                             sort_interval=p.sort_interval, history=512), device="cuda:0")
     run.init(x32, v32)
     run.step_n(steps)
     x, v = run.get_state()
@@ -92,9 +92,40 @@ def test_batched_equals_alone(variant, cluster, block, ncell_max):
         assert_same(pool, s, alone(p, x, v, steps), steps)
 
 
+@pytest.mark.parametrize("variant,cluster,block,ncell_max,intervals",
+                         [(1 + 16, 8, 256, 2048, (5, 3, 1, 7)), (5, 4, 512, 2048, (4, 9)),
+                          (2, 2, 512, 1024, (6,)), (6, 1, 512, 512, (2, 5))])
+def test_batched_with_sorting_equals_alone(variant, cluster, block, ncell_max, intervals):
+    # Runs that sort every S steps (S differing between runs, sorts falling
+    # on both sides of launch boundaries) give the same particles, density
+    # and field as the same runs alone, bit for bit: the in-cluster counting
+    # sort yields the unique stable order by cell of the single run's sort.
+    runs = [r for r in run_set() if r[0].ncell <= ncell_max]
+    for i, (p, _, _) in enumerate(runs):
+        p.sort_interval = intervals[i % len(intervals)]
+    steps = 23
+    pool = pic.Pool(max_slots=16, ncell_max=ncell_max, arena_bytes=GIB, history=512,
+                    variant=variant, cluster=cluster, block=block, device="cuda:0")
+    slots = [pool.admit(p, x, v, steps) for p, x, v in runs]
+    assert None not in slots
+    pool.advance(3)
+    pool.advance(8)
+    pool.advance(100)
+    for (p, x, v), s in zip(runs, slots):
+        assert pool.step_count(s) == steps
+        assert_same(pool, s, alone(p, x, v, steps), steps)
+
+
+def test_pool_sort_needs_a_second_buffer():
+    p = pic.Params(npart=100000, ncell=256, length=L4PI)
+    q = pic.Params(npart=100000, ncell=256, length=L4PI, sort_interval=20)
+    assert pic.pool_run_bytes(q, 64) - pic.pool_run_bytes(p, 64) >= 8 * 100000
+
+
 def test_staggered_admission_equals_alone():
     # requests admitted while others are mid-run (continuous batching)
     runs = run_set()[:5]
+    runs[1][0].sort_interval = 4           # one run sorts
     pool = pic.Pool(max_slots=8, ncell_max=2048, arena_bytes=GIB, history=512, device="cuda:0")
     plan = [(0, 30), (1, 17), (2, 25), (3, 9), (4, 12)]
     slots = {}
