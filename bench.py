@@ -20,7 +20,9 @@ FP64 oracle on this host.
 workload: each step is the oracle's step over a bounded sample, the same
 recipe (cells, box, beams, modes, seed) at 2^20 electrons.
 Under torchrun each rank runs its own independent run (weak scaling, no
-collective on the data path).
+collective on the data path: `value`); the line adds `sharded`, the same
+2^26-particle run split over the ranks with one int64 all-reduce of the
+density per step (strong scaling).
 """
 from __future__ import annotations
 
@@ -227,11 +229,18 @@ def time_ours(args, w, x32, v32):
 
     for _ in range(args.warmup):
         one_step()
+    sort_tune = None
     if not args.no_tune and not args.variant:
         # tune on the state after the warm-up (past a sort), then re-warm
         run.autotune(reps=8)
         for _ in range(3):
             one_step()
+        if S > 0:
+            # the sort-interval tuner's model for this state, reported beside
+            # the workload's own interval (which the run keeps)
+            best, table = run.tune_sort_interval((0, 5, 10, 20, 40, 80), adopt=False)
+            sort_tune = {"best": best, "ms_per_step": {str(k): round(t, 4) for k, t in table.items()},
+                         "kept": S}
     torch.cuda.synchronize()
     K = args.steps
     # the step loop through the public API: pic_step_n replays CUDA graphs of
@@ -293,7 +302,7 @@ def time_ours(args, w, x32, v32):
                launches=timed_launches,
                grid=grid, block=block, variant=variant, unroll=unroll,
                blocks_per_sm=grid // max(1, torch.cuda.get_device_properties(0).multi_processor_count),
-               steps=K,
+               steps=K, sort_tune=sort_tune,
                energy=float(diag["kinetic"] + diag["field"]))
     run.close()
     return res
@@ -333,6 +342,42 @@ def time_e2e(args, w, x32, v32):
     h2d = 2 * 4 * n
     d2h = 2 * 4 * n + d.nbytes
     return dict(value=n * K / el, seconds=el, h2d_per_step=h2d / K, d2h_per_step=d2h / K)
+
+
+def time_sharded(args, w, x32, v32):
+    """Config 2 as one plasma sharded by particles over the ranks (strong
+    scaling: the whole job is the same 2^26 particles at any N): each rank
+    holds 1/N of them and the whole grid, and every step all-reduces the
+    int64 density sums (NCCL) between its push and its solve.  Timed over K
+    steps with CUDA events, between barriers; the slowest rank's time."""
+    import torch
+    import paper_1108_1954_gb300 as pic
+    from paper_1108_1954_gb300 import shard
+    ws, rank, _ = dist_env()
+    n, S, K = w["npart"], w["sort_interval"], args.steps
+    lo, hi = shard.split(n, ws, rank)
+    sh = shard.Shard(pic.Params(npart=hi - lo, ncell=w["ncell"], length=w["length"], dt=w["dt"],
+                                sort_interval=S, history=max(64, K + 1)),
+                     n, shard.torch_allreduce(), device="cuda")
+    sh.init(x32[lo:hi], v32[lo:hi])
+    sh.step_n(max(3, args.warmup))
+    stream = sh.run.stream
+    e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+    torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sh.step_n(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    torch.distributed.barrier()
+    t = torch.tensor([e0.elapsed_time(e1) / 1e3], device="cuda", dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_s = float(t.item())                   # the slowest rank
+    sh.close()
+    return {"value": n * K / total_s, "unit": "particle-steps/s", "scaling": "strong",
+            "npart_total": n, "npart_per_rank": hi - lo, "steps": K,
+            "ms_per_step": 1e3 * total_s / K,
+            "collective": "one all-reduce (sum) of %d int64 density sums per step" % w["ncell"]}
 
 
 def ensemble_states(nrun, seed):
@@ -852,6 +897,7 @@ def main():
         return
     x32, v32 = make_state(w)
     res = time_ours(args, w, x32, v32)
+    sharded = time_sharded(args, w, x32, v32) if ws > 1 else None
     e2e = None if args.no_e2e else time_e2e(args, w, x32, v32)
     c1 = None if args.no_c1 else time_c1(args)
     batched = None if args.no_batched else time_batched(args)
@@ -886,7 +932,8 @@ def main():
                    "l2": "inputs larger than L2 (%.0f MiB particle state)" % (16 * n / 2**20 / 2),
                    "launch": {"grid": res["grid"], "block": res["block"],
                               "deposit_variant": res["variant"], "unroll": res["unroll"],
-                              "blocks_per_sm": res["blocks_per_sm"]}},
+                              "blocks_per_sm": res["blocks_per_sm"]},
+                   "sort_interval_tuner": res["sort_tune"]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": recorded_traffic(),
                      "kernel": "pic_push_fixed_kernel", "peak_source": src,
@@ -917,6 +964,8 @@ def main():
                        "d2h_bytes_per_step": e2e["d2h_per_step"]}
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if sharded is not None:
+        line["sharded"] = {k: sig(v) for k, v in sharded.items()}
     # the sections of the metric beyond the single run come last, compact,
     # so that the end of the line carries them: weak scaling, config 1, the
     # precision study, batched vs plain, served latency

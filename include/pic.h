@@ -348,6 +348,45 @@ int pic_autotune(pic_run *run, int32_t reps, pic_tune_entry *results,
                  int32_t max_results, int32_t *nresults);
 
 /* ------------------------------------------------------------------------
+ * One plasma on several GPUs, sharded by particles (the paper decomposes the
+ * line over its threads and reduces the density and the solver's sums every
+ * cycle, Sec. 3.1-3.3; here every rank keeps the whole grid).  Rank w holds
+ * N_w of the N particles in its own run.  A step is, on every rank: [its own
+ * sort when due] + pic_push + an all-reduce (sum, int64) of the NG density
+ * sums pic_device_density points at + pic_solve_field.  The sums are exact
+ * integers, so every rank solves the same density into the same field, and
+ * the shards' particles are those of the whole run bit for bit.  The start:
+ * pic_init of each rank's particles, then pic_deposit + the all-reduce +
+ * pic_solve_field to make E^0 from the whole density.  The history rows'
+ * kinetic energy and momentum are the rank's shares (sum them over the
+ * ranks); the field rows are the whole plasma's.  pic_step_n cannot take
+ * the all-reduce: step a shard with pic_push / pic_solve_field.
+ * ------------------------------------------------------------------------ */
+
+/* The run is one rank's shard of a plasma of npart_total particles
+ * (npart <= npart_total <= 2^39): the density, the particle charge and mass
+ * are normalised by npart_total.  PIC_FP32_FIXED only.  Drops the captured
+ * graphs. */
+int pic_set_shard(pic_run *run, int64_t npart_total);
+
+/* Device pointer of the density accumulator: NG int64 fixed-point sums, the
+ * deposit of the particles pushed since the last solve (PIC_FP32_FIXED). */
+int pic_device_density(pic_run *run, void **rho_q);
+
+/* Tune the sort interval S (PIC_FP32_FIXED): for each candidate in
+ * intervals[count] (0 = never sort, else 1 .. 256; count <= 64), the mean
+ * cost of a step's sort and push, modelled on a copy of the state with the
+ * run's push shape: the sort of the state is timed, then the sorted copy is
+ * pushed max(S) times with the current field, each push timed (t(k), k pushes
+ * after a sort); cost(S) = (t_sort + sum_{k<S} t(k)) / S, cost(0) = the mean
+ * of the last quarter of t(k).  ms_per_step[count] (may be NULL) receives the
+ * costs, *best (may be NULL) the cheapest candidate; adopt != 0 sets the
+ * run's sort interval to it (dropping the captured graphs).  The run's state
+ * is untouched.  Synchronises.  PIC_ESTATE as for pic_autotune. */
+int pic_tune_sort_interval(pic_run *run, const int32_t *intervals, int32_t count,
+                           float *ms_per_step, int32_t *best, int32_t adopt);
+
+/* ------------------------------------------------------------------------
  * Ensembles: many independent runs in one persistent launch (the batched and
  * served forms of the same step).  A pool owns a caller-provided device arena
  * and up to max_slots runs.  Every run's step is the step above, bit-identical

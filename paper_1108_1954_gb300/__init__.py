@@ -99,6 +99,10 @@ _SIG = {
                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "pic_autotune": (C.c_int, [_VP, C.c_int32, _VP, C.c_int32, C.POINTER(C.c_int32)]),
     "pic_set_launch": (C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
+    "pic_set_shard": (C.c_int, [_VP, C.c_int64]),
+    "pic_device_density": (C.c_int, [_VP, C.POINTER(_VP)]),
+    "pic_tune_sort_interval": (C.c_int, [_VP, _VP, C.c_int32, _VP, C.POINTER(C.c_int32),
+                                         C.c_int32]),
     "pic_phase_space": (C.c_int, [_VP, C.c_int32, C.c_int32, C.c_double, C.c_double, _VP]),
     "pic_load_two_stream": (C.c_int, [_VP, C.c_int64, C.c_double, _VP, _VP, _VP]),
     "pic_init_loaded": (C.c_int, [_VP, _VP]),
@@ -361,6 +365,32 @@ class Run:
         _check(_lib.pic_autotune(self._h, int(reps), _VP(out.ctypes.data), 64, C.byref(n)),
                "pic_autotune")
         return out[:n.value]
+
+    def set_shard(self, npart_total: int):
+        """This run holds one rank's particles of a plasma of npart_total."""
+        _check(_lib.pic_set_shard(self._h, int(npart_total)), "pic_set_shard")
+
+    def density(self):
+        """Torch int64 view of the device density accumulator (NG sums)."""
+        import torch
+        d = _VP()
+        _check(_lib.pic_device_density(self._h, C.byref(d)), "pic_device_density")
+        off = d.value - self.workspace.data_ptr()
+        return self.workspace[off:off + 8 * self.p.ncell].view(torch.int64)
+
+    def tune_sort_interval(self, intervals=(0, 5, 10, 20, 40, 80), adopt: bool = False):
+        """Modelled step cost (ms) of each candidate sort interval on a copy
+        of the state; returns (best interval, {S: ms}).  adopt: make the run
+        sort at the best interval from now on."""
+        iv = np.ascontiguousarray(intervals, dtype=np.int32)
+        ms = np.zeros(iv.size, dtype=np.float32)
+        best = C.c_int32(0)
+        _check(_lib.pic_tune_sort_interval(self._h, _VP(iv.ctypes.data), iv.size,
+                                           _VP(ms.ctypes.data), C.byref(best), int(adopt)),
+               "pic_tune_sort_interval")
+        if adopt:
+            self.p.sort_interval = int(best.value)
+        return int(best.value), {int(k): float(t) for k, t in zip(iv, ms)}
 
     def launch_shape(self):
         """(grid, block, variant, unroll) of the fused push."""

@@ -158,6 +158,7 @@ struct pic_run {
     PushConsts pc{};
     double dx = 0, mass = 0, q_over_dx = 0, k_rho = 0, k_e = 0, k_phi = 0;
     double to_cells = 0, to_phys = 0;  // NG/L and L/NG (float32 positions)
+    int64_t npart_total = 0;           // particles of the whole plasma (a shard holds npart)
     float length32 = 0;                // (float)L: positions lie in [0, length32)
 
     template <typename T> T *at(size_t off) const { return reinterpret_cast<T *>(ws + off); }
@@ -168,6 +169,20 @@ struct pic_run {
 };
 
 namespace {
+
+// Float64 constants of the solve for a plasma of n_total particles (Appendix
+// A: Q0 = rho_init0 Lx / N, with the sign of qm; a shard holds n of them).
+void set_solve_constants(pic_run *r, int64_t n_total) {
+    const pic_params *p = &r->p;
+    r->npart_total = n_total;
+    r->dx = p->length / (double)p->ncell;
+    const double q0 = (p->rho_ion * p->length / (double)n_total) * (p->qm / std::fabs(p->qm));
+    r->q_over_dx = q0 / r->dx;
+    r->mass = q0 / p->qm;
+    r->k_rho = p->rho_ion / std::ldexp((double)n_total, kFixBits);
+    r->k_e = 0.5 * r->dx * r->k_rho / (double)p->ncell;
+    r->k_phi = -r->dx * r->dx * r->k_rho / (double)p->ncell;
+}
 
 void destroy_graphs(pic_run *r) {
     for (auto &g : r->period)
@@ -236,7 +251,7 @@ cudaError_t enqueue_solve(pic_run *r, cudaStream_t s, bool after_push) {
     a.hist_len = r->lay.hist_len;
     a.dstep = &r->dev()->step;
     a.ng = r->p.ncell;
-    a.weight_total = (long long)r->p.npart << kFixBits;
+    a.weight_total = (long long)r->npart_total << kFixBits;
     a.rho_ion = r->p.rho_ion;
     a.q_over_dx = r->q_over_dx;
     a.k_rho = r->k_rho;
@@ -449,14 +464,7 @@ int pic_create(const pic_params *p, void *workspace, size_t workspace_bytes,
     r->to_cells = (double)p->ncell / p->length;
     r->to_phys = p->length / (double)p->ncell;
     r->length32 = (float)p->length;
-    // float64 constants of the solve (Appendix A: Q0 = rho_init0 Lx / N, sign of qm)
-    r->dx = p->length / (double)p->ncell;
-    const double q0 = (p->rho_ion * p->length / (double)p->npart) * (p->qm / std::fabs(p->qm));
-    r->q_over_dx = q0 / r->dx;
-    r->mass = q0 / p->qm;
-    r->k_rho = p->rho_ion / std::ldexp((double)p->npart, kFixBits);
-    r->k_e = 0.5 * r->dx * r->k_rho / (double)p->ncell;
-    r->k_phi = -r->dx * r->dx * r->k_rho / (double)p->ncell;
+    set_solve_constants(r, p->npart);
 
     // launch shape of the fused push
     r->variant = p->deposit_variant ? p->deposit_variant : PIC_DEPOSIT_QUAD;
@@ -807,6 +815,101 @@ done:
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
+    PIC_CUDA(cudaMemsetAsync(run->ws + run->lay.tune_rho, 0, (size_t)run->p.ncell * 8, run->stream));
+    return read_error_word(run);
+}
+
+int pic_set_shard(pic_run *run, int64_t npart_total) {
+    if (!run) return PIC_EINVAL;
+    if (run->p.precision != PIC_FP32_FIXED) return PIC_EINVAL;
+    if (npart_total < run->p.npart || npart_total > ((int64_t)1 << 39)) return PIC_EINVAL;
+    if (run->pending_push) return PIC_ESTATE;
+    set_solve_constants(run, npart_total);
+    destroy_graphs(run);
+    return PIC_OK;
+}
+
+int pic_device_density(pic_run *run, void **rho_q) {
+    if (!run || !rho_q) return PIC_EINVAL;
+    if (run->p.precision != PIC_FP32_FIXED) return PIC_EINVAL;
+    *rho_q = run->ws + run->lay.rho_q;
+    return PIC_OK;
+}
+
+// Sort-interval tuner: the mean cost of a step's sort and push for each
+// candidate S, modelled from measurements on a copy of the state.  The sort
+// of the state into the idle buffer is timed, then the sorted copy is pushed
+// kmax times with the current field (the particles drift apart as they do
+// between sorts) and each push is timed: t(k), k pushes after a sort.  For
+// S > 0 the cost is (t_sort + sum_{k<S} t(k)) / S; for S = 0 (never sort) it
+// is the mean of the last quarter of t(k), the drifted state.  The run's own
+// state is untouched (the copy's pushes deposit into the tuning density).
+int pic_tune_sort_interval(pic_run *run, const int32_t *intervals, int32_t count,
+                           float *ms_per_step, int32_t *best, int32_t adopt) {
+    if (!run || !intervals || count < 1 || count > 64) return PIC_EINVAL;
+    if (run->p.precision != PIC_FP32_FIXED) return PIC_EINVAL;
+    int kmax = 8;
+    for (int i = 0; i < count; i++) {
+        if (intervals[i] < 0 || intervals[i] > 256) return PIC_EINVAL;
+        if (intervals[i] > kmax) kmax = intervals[i];
+    }
+    if (!run->ready || run->pending_push) return PIC_ESTATE;
+    const int c = run->cur;
+    cudaEvent_t ev[2 * 257 + 2];
+    const int nev = 2 * kmax + 2;
+    int made = 0;
+    int rc = PIC_OK;
+    cudaError_t e = cudaSuccess;
+    for (; made < nev && e == cudaSuccess; made++) e = cudaEventCreate(&ev[made]);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], run->stream);
+    if (e == cudaSuccess) e = enqueue_sort_into(run, c, run->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], run->stream);
+    PushArgs a;
+    a.x = (float *)run->xs(1 - c);
+    a.v = (float *)run->vs(1 - c);
+    a.n = run->p.npart;
+    a.E32 = run->at<float>(run->lay.E32);
+    a.rho_q = run->at<unsigned long long>(run->lay.tune_rho);
+    a.partials = run->at<double>(run->lay.partials);
+    a.err = &run->dev()->err;
+    a.c = run->pc;
+    for (int k = 0; k < kmax && e == cudaSuccess; k++) {
+        e = cudaEventRecord(ev[2 + 2 * k], run->stream);
+        if (e == cudaSuccess)
+            e = launch_push_fixed(a, run->grid, run->block, run->variant, run->unroll, true,
+                                  run->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[3 + 2 * k], run->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(run->stream);
+    float tsort = 0.0f, t[256];
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&tsort, ev[0], ev[1]);
+    for (int k = 0; k < kmax && e == cudaSuccess; k++)
+        e = cudaEventElapsedTime(&t[k], ev[2 + 2 * k], ev[3 + 2 * k]);
+    if (e != cudaSuccess) rc = cuda_fail(e);
+    for (int i = 0; i < made; i++) cudaEventDestroy(ev[i]);
+    if (rc) return rc;
+    float drift = 0.0f;
+    const int q0 = kmax - kmax / 4;
+    for (int k = q0; k < kmax; k++) drift += t[k];
+    drift /= (float)(kmax - q0);
+    int bi = 0;
+    float bcost = 0.0f;
+    for (int i = 0; i < count; i++) {
+        const int S = intervals[i];
+        float cost = drift;
+        if (S > 0) {
+            cost = tsort;
+            for (int k = 0; k < S; k++) cost += t[k];
+            cost /= (float)S;
+        }
+        if (ms_per_step) ms_per_step[i] = cost;
+        if (i == 0 || cost < bcost) { bi = i; bcost = cost; }
+    }
+    if (best) *best = intervals[bi];
+    if (adopt && run->p.sort_interval != intervals[bi]) {
+        run->p.sort_interval = intervals[bi];
+        destroy_graphs(run);
+    }
     PIC_CUDA(cudaMemsetAsync(run->ws + run->lay.tune_rho, 0, (size_t)run->p.ncell * 8, run->stream));
     return read_error_word(run);
 }

@@ -217,3 +217,33 @@ def test_sort_matches_stable_argsort(layout):
     run.sort()
     xs2, vs2 = run.get_cells()
     assert np.array_equal(xs2, xs) and np.array_equal(vs2, vs)
+
+
+def test_sort_interval_tuner_leaves_the_state_and_adopts():
+    n, ng = 400003, 1024
+    x, v = W.two_stream(n, L4PI, 0.2, 0.01, 21)
+    x32, v32 = W.to_f32_state(x, v, L4PI)
+    a = make_run(n, ng, L4PI, sort_interval=10)
+    b = make_run(n, ng, L4PI, sort_interval=10)
+    a.init(x32, v32)
+    b.init(x32, v32)
+    a.step_n(13)
+    b.step_n(13)
+    best, table = a.tune_sort_interval((0, 3, 10, 40), adopt=False)
+    assert best in (0, 3, 10, 40) and set(table) == {0, 3, 10, 40}
+    assert all(t > 0 for t in table.values())
+    assert table[best] == min(table.values())
+    assert a.p.sort_interval == 10
+    ua, va = a.get_cells()
+    ub, vb = b.get_cells()
+    assert np.array_equal(ua, ub) and np.array_equal(va, vb)
+    # adopting: the run then sorts at the chosen interval, exactly like a run
+    # created with it from the same state
+    best, _ = a.tune_sort_interval((3,), adopt=True)
+    assert best == 3 and a.p.sort_interval == 3
+    c = make_run(n, ng, L4PI, sort_interval=3)
+    c.set_cells(ua, va, 13)
+    a.step_n(11)
+    c.step_n(11)
+    assert np.array_equal(a.get_cells()[0], c.get_cells()[0])
+    assert np.array_equal(a.get_field()["rho_q"], c.get_field()["rho_q"])
