@@ -533,13 +533,21 @@ def precision_study(args):
     out = {"npart": n, "ncell": ng, "steps": K, "gamma_theory": W.cold_two_stream_gamma(2 * math.pi / L, 0.2)}
     ref = O.State(O.params(ng, n, L, dt), x32.astype(np.float64), v32.astype(np.float64))
     t0 = time.perf_counter()
-    h = ref.run(args.precision_oracle_steps)
+    nt = host_threads()
+    ko_ = args.precision_oracle_steps
+    h = np.zeros((ko_, 11))
+    for k in range(ko_):
+        # the history row of orc_run, with the threaded step (same state)
+        h[k, 2] = O.field_energy(ref.p, ref.E)
+        h[k, 3:] = O.mode_amplitudes(ref.p, ref.E, 8)
+        h[k, 0], h[k, 1] = ref.step_threads(nt) if nt > 1 else ref.step()
     o_fe = h[:, 2]
     o_ke = 0.5 * ref.mass * h[:, 0]
     ko = args.precision_oracle_steps
     fo = fit[:ko]
     o_gamma = float(np.polyfit(t[:ko][fo], np.log(h[fo, 3]), 1)[0]) if fo.sum() > 4 else None
-    out["oracle"] = {"steps": ko, "seconds": time.perf_counter() - t0, "gamma1": o_gamma}
+    out["oracle"] = {"steps": ko, "seconds": time.perf_counter() - t0, "gamma1": o_gamma,
+                     "threads": nt}
     for name, mode, xs, vs in (("fp64", pic.PIC_FP64, x, v),
                                ("fp32_atomic", pic.PIC_FP32_ATOMIC, x32, v32),
                                ("fp32_fixed", pic.PIC_FP32_FIXED, x32, v32)):
@@ -772,9 +780,29 @@ def time_served(args):
     return stats
 
 
-def time_oracle(w, x32, v32, budget_s=12.0, sample=None, steps=None):
-    """The FP64 oracle, single thread, on the same state (or its first
-    `sample` particles): particle-steps/s."""
+def host_threads():
+    """The host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def time_oracle(w, x32, v32, budget_s=12.0, sample=None, steps=None, threads=1):
+    """The FP64 oracle on the same state (or its first `sample` particles):
+    particle-steps/s, on one thread (orc_step) or on `threads` host threads
+    (orc_step_threads, the same state bit for bit)."""
     import numpy as np
     import oracle as O
     n = w["npart"] if sample is None else min(sample, w["npart"])
@@ -783,14 +811,17 @@ def time_oracle(w, x32, v32, budget_s=12.0, sample=None, steps=None):
     st = O.State(O.params(w["ncell"], n, w["length"], w["dt"]), x, v)
     done, t0 = 0, time.perf_counter()
     while True:
-        st.step()
+        if threads > 1:
+            st.step_threads(threads)
+        else:
+            st.step()
         done += 1
         el = time.perf_counter() - t0
         if steps is not None and done >= steps:
             break
         if steps is None and el >= budget_s:
             break
-    return dict(value=n * done / el, steps=done, npart=n, seconds=el)
+    return dict(value=n * done / el, steps=done, npart=n, seconds=el, threads=threads)
 
 
 def sig(x, digits=4):
@@ -855,8 +886,9 @@ def main():
         ws_ = dict(w, npart=min(REF_SAMPLE, w["npart"]))
         x32, v32 = make_state(ws_)
         K, Wm = args.steps, args.warmup
-        time_oracle(ws_, x32, v32, steps=max(1, Wm))
-        r = time_oracle(ws_, x32, v32, steps=max(1, K))
+        nt = host_threads()
+        time_oracle(ws_, x32, v32, steps=max(1, Wm), threads=nt)
+        r = time_oracle(ws_, x32, v32, steps=max(1, K), threads=nt)
         line = {
             "impl": "reference", "metric": "particle-steps/s",
             "value": r["value"], "unit": "particle-steps/s", "n_gpus": args.gpus,
@@ -865,11 +897,11 @@ def main():
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": "single large run, %d electrons, %d cells (oracle sample %d)"
                        % (w["npart"], w["ncell"], r["npart"])},
-            "cpu_baseline": {"value": r["value"], "unit": "particle-steps/s", "cores": 1,
-                             "kind": "oracle",
-                             "sample": "FP64 oracle, the same recipe at %d electrons "
-                                       "(cells, box, beams, modes unchanged), %d steps"
-                             % (r["npart"], r["steps"])},
+            "cpu_baseline": {"value": r["value"], "unit": "particle-steps/s", "cores": nt,
+                             "kind": "oracle", "cpu": cpu_model(),
+                             "sample": "FP64 oracle on %d host threads, the same recipe at %d "
+                                       "electrons (cells, box, beams, modes unchanged), %d steps"
+                             % (nt, r["npart"], r["steps"])},
             "e2e": {"value": r["value"], "unit": "particle-steps/s",
                     "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         }
@@ -912,10 +944,16 @@ def main():
     peak, src = measured_peak()
     cpu = None
     if rank == 0 and not args.no_cpu:
-        c = time_oracle(w, x32, v32, budget_s=12.0)
-        cpu = {"value": c["value"], "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-               "sample": "FP64 oracle on the full %d-particle state, first %d steps (%.1f s)"
-               % (c["npart"], c["steps"], c["seconds"])}
+        nt = host_threads()
+        c1 = time_oracle(w, x32, v32, budget_s=10.0)
+        c = time_oracle(w, x32, v32, budget_s=10.0, threads=nt) if nt > 1 else c1
+        cpu = {"value": c["value"], "unit": "particle-steps/s", "cores": nt, "kind": "oracle",
+               "cpu": cpu_model(),
+               "sample": "FP64 oracle on the full %d-particle state, first %d steps (%.1f s) on "
+                         "%d host threads" % (c["npart"], c["steps"], c["seconds"], nt),
+               "value_1core": c1["value"],
+               "sample_1core": "the same on one thread: first %d steps (%.1f s)"
+                               % (c1["steps"], c1["seconds"])}
     if rank != 0:
         torch.distributed.destroy_process_group()
         return

@@ -34,7 +34,7 @@ def build(force: bool = False) -> str:
         return _LIB
     tmp = _LIB + ".%d.tmp" % os.getpid()
     cmd = ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math",
-           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+           "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
@@ -80,6 +80,8 @@ def _load():
                 "orc_field": (C.c_int, [_P, _D, _D, _D, _D]),
                 "orc_prepare": (C.c_int, [_P, _D, _D, _D, _D, _D]),
                 "orc_step": (C.c_int, [_P, _D, _D, _D, _D, _D, _D, _D]),
+                "orc_step_threads": (C.c_int, [_P, _D, _D, _D, _D, _D, _D, _D,
+                                               C.POINTER(C.c_int32), C.c_int]),
                 "orc_run_paper_order": (C.c_int, [_P, _D, _D, _D, _D, _D,
                                                   C.c_int64, _D]),
                 "orc_run": (C.c_int, [_P, _D, _D, _D, _D, _D, C.c_int64,
@@ -143,6 +145,19 @@ class State:
         _check(_load().orc_step(C.byref(self.p), _d(self.x), _d(self.v),
                                 _d(self.rho), _d(self.phi), _d(self.E),
                                 _d(self._work), _d(sums)), "step")
+        return float(sums[0]), float(sums[1])
+
+    def step_threads(self, nthreads: int):
+        """orc_step on nthreads host threads (the same state bit for bit; the
+        two sums grouped by thread).  For timing the oracle on all cores."""
+        if getattr(self, "_ig", None) is None:
+            self._ig = np.zeros(self.p.np, dtype=np.int32)
+        sums = np.zeros(2)
+        _check(_load().orc_step_threads(C.byref(self.p), _d(self.x), _d(self.v),
+                                        _d(self.rho), _d(self.phi), _d(self.E),
+                                        _d(self._work), _d(sums),
+                                        self._ig.ctypes.data_as(C.POINTER(C.c_int32)),
+                                        int(nthreads)), "threaded step")
         return float(sums[0]), float(sums[1])
 
     def run(self, nsteps: int, nmodes: int = 8) -> np.ndarray:

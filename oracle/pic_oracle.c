@@ -40,6 +40,7 @@
  * Build: plain C99, -O2 -ffp-contract=off (no fused multiply-add, so float
  * and double expressions round exactly as written).
  */
+#define _POSIX_C_SOURCE 200809L
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -119,6 +120,30 @@ static int orc_deposit_ngp(const orc_params *p, const double *xp, double *rho)
     return ORC_OK;
 }
 
+/* The linear weighting of one particle at x (Sec. 2.3, reading R2):
+ * ig = trunc(x/dx + 1/2); node *a (the node at or above x) takes w2 = 1 - w1
+ * and node *b (the one below) w1 = (xg[a] - x)/dx, with the periodic ends
+ * (ig = 0: a = 0, b = NG-1; ig = NG: a = NG-1, b = 0, the weights measured
+ * from the last centre).  Returns ig. */
+static int orc_cic(const orc_params *p, double x, double dx, double xg_last,
+                   int *a, int *b, double *w1, double *w2)
+{
+    const int ng = p->ng;
+    int ig = (int)(x / dx + 0.5);
+    if (ig == 0) {
+        *w1 = (dx / 2.0 - x) / dx; *w2 = 1 - *w1;
+        *a = 0; *b = ng - 1;
+    } else if (ig >= ng) {
+        *w1 = (x - xg_last) / dx; *w2 = 1 - *w1;
+        *a = ng - 1; *b = 0;
+    } else {
+        double xg = dx / 2.0 + dx * ig;
+        *w1 = (xg - x) / dx; *w2 = 1 - *w1;
+        *a = ig; *b = ig - 1;
+    }
+    return ig;
+}
+
 int orc_deposit(const orc_params *p, const double *xp, double *rho)
 {
     if (p->shape == ORC_NGP) return orc_deposit_ngp(p, xp, rho);
@@ -129,19 +154,11 @@ int orc_deposit(const orc_params *p, const double *xp, double *rho)
     for (int64_t ip = 0; ip < p->np; ip++) {
         double x = xp[ip];
         if (!(x >= 0.0 && x <= p->lx)) return ORC_ERANGE;
-        int ig = (int)(x / dx + 0.5);
+        int a, b;
         double w1, w2;
-        if (ig == 0) {
-            w1 = (dx / 2.0 - x) / dx; w2 = 1 - w1;
-            rho[0] += w2 * Q0 / dx; rho[ng - 1] += w1 * Q0 / dx;
-        } else if (ig >= ng) {
-            w1 = (x - xg_last) / dx; w2 = 1 - w1;
-            rho[ng - 1] += w2 * Q0 / dx; rho[0] += w1 * Q0 / dx;
-        } else {
-            double xg = dx / 2.0 + dx * ig;
-            w1 = (xg - x) / dx; w2 = 1 - w1;
-            rho[ig] += w2 * Q0 / dx; rho[ig - 1] += w1 * Q0 / dx;
-        }
+        orc_cic(p, x, dx, xg_last, &a, &b, &w1, &w2);
+        rho[a] += w2 * Q0 / dx;
+        rho[b] += w1 * Q0 / dx;
     }
     return ORC_OK;
 }
@@ -250,19 +267,10 @@ int orc_gather(const orc_params *p, const double *xp, const double *E,
     for (int64_t ip = 0; ip < p->np; ip++) {
         double x = xp[ip];
         if (!(x >= 0.0 && x <= p->lx)) return ORC_ERANGE;
-        int ig = (int)(x / dx + 0.5);
+        int a, b;
         double w1, w2;
-        if (ig == 0) {
-            w1 = (dx / 2.0 - x) / dx; w2 = 1 - w1;
-            Ex[ip] = w2 * E[0] + w1 * E[ng - 1];
-        } else if (ig >= ng) {
-            w1 = (x - xg_last) / dx; w2 = 1 - w1;
-            Ex[ip] = w2 * E[ng - 1] + w1 * E[0];
-        } else {
-            double xg = dx / 2.0 + dx * ig;
-            w1 = (xg - x) / dx; w2 = 1 - w1;
-            Ex[ip] = w2 * E[ig] + w1 * E[ig - 1];
-        }
+        orc_cic(p, x, dx, xg_last, &a, &b, &w1, &w2);
+        Ex[ip] = w2 * E[a] + w1 * E[b];
     }
     return ORC_OK;
 }
@@ -321,6 +329,137 @@ int orc_step(const orc_params *p, double *xp, double *vp, double *rho,
     if (sums) { sums[0] = svv; sums[1] = sv; }
     orc_drift(p, vp, xp);
     return orc_prepare(p, xp, rho, phi, E, fw);
+}
+
+/* ---------------------------------------------------------------------
+ * orc_step on several host threads, for timing the oracle on all cores.
+ * The state it leaves (x, v, rho, phi, E) is bit for bit that of orc_step:
+ *   - the gather, kick, drift and wrap of each particle are the serial
+ *     code's operations on that particle, the particles split in ranges;
+ *   - the deposit is split by nodes, not particles: each thread owns a
+ *     range of nodes, scans every particle in order and adds only to its
+ *     own nodes, so every node receives the serial code's additions in the
+ *     serial order;
+ *   - the field solve is the serial one.
+ * Only the two sums (sum v_old v_new, sum v_new) add the same terms in
+ * another grouping (per thread range, then over the ranges in order).
+ * CIC shape only.  ig: NP ints of work.
+ * --------------------------------------------------------------------- */
+#include <pthread.h>
+
+typedef struct {
+    const orc_params *p;
+    double *xp, *vp;
+    const double *E;
+    int32_t *ig;
+    int64_t lo, hi;
+    double svv, sv;
+    int rc;
+} orc_push_job;
+
+static void *orc_push_range(void *arg)
+{
+    orc_push_job *j = (orc_push_job *)arg;
+    const orc_params *p = j->p;
+    const double dx = orc_dx(p);
+    const double xg_last = dx / 2.0 + dx * (p->ng - 1);
+    double svv = 0.0, sv = 0.0;
+    j->rc = ORC_OK;
+    for (int64_t ip = j->lo; ip < j->hi; ip++) {
+        double x = j->xp[ip];
+        if (!(x >= 0.0 && x <= p->lx)) { j->rc = ORC_ERANGE; return NULL; }
+        int a, b;
+        double w1, w2;
+        orc_cic(p, x, dx, xg_last, &a, &b, &w1, &w2);
+        double Ex = w2 * j->E[a] + w1 * j->E[b];
+        double vold = j->vp[ip];
+        j->vp[ip] = vold + p->qoms0 * Ex * p->dt;
+        svv += vold * j->vp[ip];
+        sv += j->vp[ip];
+        x = orc_wrap(j->xp[ip] + j->vp[ip] * p->dt, p->lx);
+        j->xp[ip] = x;
+        if (!(x >= 0.0 && x <= p->lx)) { j->rc = ORC_ERANGE; return NULL; }
+        j->ig[ip] = (int32_t)(x / dx + 0.5);
+    }
+    j->svv = svv;
+    j->sv = sv;
+    return NULL;
+}
+
+typedef struct {
+    const orc_params *p;
+    const double *xp;
+    const int32_t *ig;
+    double *rho;
+    int g0, g1;
+} orc_dep_job;
+
+/* Does a particle with this ig touch a node in [g0, g1)? (the nodes orc_cic
+ * picks: ig and ig-1, NG-1 for ig = 0, 0 and NG-1 for ig >= NG) */
+static int orc_touches(int ig, int ng, int g0, int g1)
+{
+    int a = ig >= ng ? ng - 1 : ig;
+    int b = ig == 0 ? ng - 1 : (ig >= ng ? 0 : ig - 1);
+    return (a >= g0 && a < g1) || (b >= g0 && b < g1);
+}
+
+static void *orc_deposit_nodes(void *arg)
+{
+    orc_dep_job *j = (orc_dep_job *)arg;
+    const orc_params *p = j->p;
+    const int ng = p->ng;
+    const double dx = orc_dx(p), Q0 = orc_q0(p);
+    const double xg_last = dx / 2.0 + dx * (ng - 1);
+    for (int ic = j->g0; ic < j->g1; ic++) j->rho[ic] = p->rho_init0;
+    for (int64_t ip = 0; ip < p->np; ip++) {
+        if (!orc_touches(j->ig[ip], ng, j->g0, j->g1)) continue;
+        int a, b;
+        double w1, w2;
+        orc_cic(p, j->xp[ip], dx, xg_last, &a, &b, &w1, &w2);
+        if (a >= j->g0 && a < j->g1) j->rho[a] += w2 * Q0 / dx;
+        if (b >= j->g0 && b < j->g1) j->rho[b] += w1 * Q0 / dx;
+    }
+    return NULL;
+}
+
+#define ORC_MAX_THREADS 256
+
+int orc_step_threads(const orc_params *p, double *xp, double *vp, double *rho,
+                     double *phi, double *E, double *work, double *sums,
+                     int32_t *ig, int nthreads)
+{
+    if (p->shape != ORC_CIC || nthreads < 1 || nthreads > ORC_MAX_THREADS)
+        return ORC_EINVAL;
+    pthread_t th[ORC_MAX_THREADS];
+    orc_push_job pj[ORC_MAX_THREADS];
+    orc_dep_job dj[ORC_MAX_THREADS];
+    int nt = nthreads;
+    for (int t = 0; t < nt; t++) {
+        pj[t].p = p; pj[t].xp = xp; pj[t].vp = vp; pj[t].E = E; pj[t].ig = ig;
+        pj[t].lo = p->np * t / nt;
+        pj[t].hi = p->np * (t + 1) / nt;
+        pj[t].svv = 0.0; pj[t].sv = 0.0;
+        if (pthread_create(&th[t], NULL, orc_push_range, &pj[t]) != 0) return ORC_EINVAL;
+    }
+    int rc = ORC_OK;
+    double svv = 0.0, sv = 0.0;
+    for (int t = 0; t < nt; t++) {
+        pthread_join(th[t], NULL);
+        if (pj[t].rc) rc = pj[t].rc;
+        svv += pj[t].svv;
+        sv += pj[t].sv;
+    }
+    if (rc) return rc;
+    if (sums) { sums[0] = svv; sums[1] = sv; }
+    int ntd = nt < p->ng ? nt : p->ng;
+    for (int t = 0; t < ntd; t++) {
+        dj[t].p = p; dj[t].xp = xp; dj[t].ig = ig; dj[t].rho = rho;
+        dj[t].g0 = (int)((int64_t)p->ng * t / ntd);
+        dj[t].g1 = (int)((int64_t)p->ng * (t + 1) / ntd);
+        if (pthread_create(&th[t], NULL, orc_deposit_nodes, &dj[t]) != 0) return ORC_EINVAL;
+    }
+    for (int t = 0; t < ntd; t++) pthread_join(th[t], NULL);
+    return orc_field(p, rho, phi, E, work + p->np);
 }
 
 /* nt cycles in the order of the Appendix A time loop and the summary of

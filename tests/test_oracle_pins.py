@@ -380,3 +380,21 @@ def test_fixed_deposit_has_no_box_scale_ramp(n, ng, lx):
         g = np.arange(1, ng - 1)
         slope = np.polyfit(g, E_fix[1:-1], 1)[0] * ng / lx
         assert abs(slope) < 0.01 * abs(eta)
+
+
+@pytest.mark.parametrize("n,ng,threads", [(20000, 64, 4), (20001, 64, 7), (3001, 1, 3),
+                                          (50000, 1024, 16), (1000, 8, 32)])
+def test_threaded_step_is_the_serial_step(n, ng, threads):
+    # The threaded step (timing on all host cores) leaves the serial step's
+    # state bit for bit: particle ranges for the push, node ranges for the
+    # deposit; only the two sums group their terms differently.
+    x, v = W.two_stream(n, L4PI, 0.2, 0.01, n + ng)
+    a = O.State(O.params(ng, n, L4PI), x, v)
+    b = O.State(O.params(ng, n, L4PI), x, v)
+    for _ in range(6):
+        sa = a.step()
+        sb = b.step_threads(threads)
+        for arr in ("x", "v", "rho", "phi", "E"):
+            assert np.array_equal(getattr(a, arr), getattr(b, arr)), arr
+        assert sa[0] == pytest.approx(sb[0], rel=1e-12)
+        assert sa[1] == pytest.approx(sb[1], rel=1e-12, abs=1e-12 * np.abs(a.v).sum())
