@@ -603,8 +603,8 @@ def variant_scan(args):
         xs, vs = run.get_cells()
         st = run.step
         row = {"step": st}
-        for var in (1, 2, 5, 6):
-            for blk, un in ((512, 1), (512, 2), (256, 1)):
+        for var in (1, 2, 5, 6, 8, 9):
+            for blk, un in ((512, 1), (512, 2), (256, 1), (256, 2)):
                 run.set_cells(xs, vs, st)
                 run.set_launch(var, blk, un)
                 ev = [(torch.cuda.Event(True), torch.cuda.Event(True)) for _ in range(2 * S)]

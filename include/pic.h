@@ -86,6 +86,12 @@ extern "C" {
 #define PIC_DEPOSIT_PAIR 6         /* QUAD with two open runs per thread, so
                                       particles of two interleaved cells (two
                                       beams before a sort) still combine    */
+#define PIC_DEPOSIT_QUAD8 8        /* QUAD over a thread's 8 consecutive
+                                      particles, moved by 32-byte vector
+                                      loads and stores (unroll: 8-particle
+                                      groups per thread per iteration, 1, 2) */
+#define PIC_DEPOSIT_PAIR8 9        /* PAIR over 8 consecutive particles, the
+                                      same loads and stores as QUAD8        */
 
 /* Field solvers (pic_params.field_solver).  Both solve the Eq. 6 system with
  * Phi_0 = 0 (the gauge the paper pins).

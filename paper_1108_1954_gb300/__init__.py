@@ -31,6 +31,7 @@ PIC_ETIMEOUT, PIC_EDEVICE, PIC_ESTATE = -4, -5, -6
 PIC_FP32_FIXED, PIC_FP32_ATOMIC, PIC_FP64 = 0, 1, 2
 PIC_DEPOSIT_AUTO, PIC_DEPOSIT_ATOMIC, PIC_DEPOSIT_MATCH = 0, 1, 2
 PIC_DEPOSIT_QUAD, PIC_DEPOSIT_PAIR = 5, 6
+PIC_DEPOSIT_QUAD8, PIC_DEPOSIT_PAIR8 = 8, 9
 PIC_SOLVER_EXACT, PIC_SOLVER_CG = 0, 1
 PIC_SHAPE_CIC, PIC_SHAPE_NGP = 0, 1
 PIC_CG_DEFAULT_ITERATIONS = 150
@@ -39,7 +40,8 @@ PIC_NMODES = 8
 FIX_BITS = 24
 
 VARIANT_NAMES = {PIC_DEPOSIT_ATOMIC: "atomic", PIC_DEPOSIT_MATCH: "match",
-                 PIC_DEPOSIT_QUAD: "quad", PIC_DEPOSIT_PAIR: "pair"}
+                 PIC_DEPOSIT_QUAD: "quad", PIC_DEPOSIT_PAIR: "pair",
+                 PIC_DEPOSIT_QUAD8: "quad8", PIC_DEPOSIT_PAIR8: "pair8"}
 
 
 class CParams(C.Structure):

@@ -126,7 +126,8 @@ __device__ __forceinline__ void deposit_one(const Tile &t, float x, bool valid,
     if (valid && !ok) atomicOr(err, kErrPosition);
     const unsigned W = ok ? fixed_weight(l.f) : 0u;
     if (VARIANT == PIC_DEPOSIT_ATOMIC || VARIANT == PIC_DEPOSIT_QUAD ||
-        VARIANT == PIC_DEPOSIT_PAIR) {
+        VARIANT == PIC_DEPOSIT_PAIR || VARIANT == PIC_DEPOSIT_QUAD8 ||
+        VARIANT == PIC_DEPOSIT_PAIR8) {
         if (ok) {
             tile_add(t, l.j, kFixOne - W);
             tile_add(t, l.j + 1, W);
@@ -144,17 +145,17 @@ __device__ __forceinline__ void deposit_one(const Tile &t, float x, bool valid,
     }
 }
 
-// Deposit the 4 particles of a float4 group (valid per lane).
-template <int VARIANT>
-__device__ __forceinline__ void deposit4(const Tile &t, const float4 &xx, bool valid,
-                                         const PushConsts &c, unsigned *err, int lane) {
-    const float xs[4] = {xx.x, xx.y, xx.z, xx.w};
+// Deposit a thread's W consecutive particles (W = 4: a float4 group; W = 8:
+// the 32-byte groups of the QUAD8 / PAIR8 variants), valid per lane.
+template <int VARIANT, int W>
+__device__ __forceinline__ void deposit_group(const Tile &t, const float (&xs)[W], bool valid,
+                                              const PushConsts &c, unsigned *err, int lane) {
     if (VARIANT == kDepositNgp) {
-        // runs of equal cell among the 4 particles: count * 2^24 per run
+        // runs of equal cell among the W particles: count * 2^24 per run
         unsigned key = 0xffffffffu, cnt = 0;
         bool bad = false;
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
+        for (int k = 0; k < W; k++) {
             const unsigned j = locate_ngp(xs[k]);
             const bool ok = valid && j - 1u <= (unsigned)c.ng;
             bad |= valid && !ok;
@@ -168,58 +169,58 @@ __device__ __forceinline__ void deposit4(const Tile &t, const float4 &xx, bool v
         }
         if (key != 0xffffffffu) tile_add(t, key, cnt);
         if (bad) atomicOr(err, kErrPosition);
-    } else if (VARIANT == PIC_DEPOSIT_PAIR) {
+    } else if (VARIANT == PIC_DEPOSIT_PAIR || VARIANT == PIC_DEPOSIT_PAIR8) {
         // two open runs (key, left, right); a third key closes run a
         unsigned ka = 0xffffffffu, la = 0, ra = 0, kb = 0xffffffffu, lb = 0, rb = 0;
         bool bad = false;
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
+        for (int k = 0; k < W; k++) {
             const Loc l = locate(xs[k]);
             const bool ok = valid && l.j <= (unsigned)c.ng;
             bad |= valid && !ok;
-            const unsigned W = fixed_weight(l.f);
+            const unsigned Wk = fixed_weight(l.f);
             if (!ok) continue;
             if (l.j == ka) {
-                la += kFixOne - W;
-                ra += W;
+                la += kFixOne - Wk;
+                ra += Wk;
             } else if (l.j == kb) {
-                lb += kFixOne - W;
-                rb += W;
+                lb += kFixOne - Wk;
+                rb += Wk;
             } else if (ka == 0xffffffffu) {
-                ka = l.j; la = kFixOne - W; ra = W;
+                ka = l.j; la = kFixOne - Wk; ra = Wk;
             } else if (kb == 0xffffffffu) {
-                kb = l.j; lb = kFixOne - W; rb = W;
+                kb = l.j; lb = kFixOne - Wk; rb = Wk;
             } else {
                 tile_add(t, ka, la);
                 tile_add(t, ka + 1, ra);
-                ka = l.j; la = kFixOne - W; ra = W;
+                ka = l.j; la = kFixOne - Wk; ra = Wk;
             }
         }
         if (ka != 0xffffffffu) { tile_add(t, ka, la); tile_add(t, ka + 1, ra); }
         if (kb != 0xffffffffu) { tile_add(t, kb, lb); tile_add(t, kb + 1, rb); }
         if (bad) atomicOr(err, kErrPosition);
-    } else if (VARIANT == PIC_DEPOSIT_QUAD) {
+    } else if (VARIANT == PIC_DEPOSIT_QUAD || VARIANT == PIC_DEPOSIT_QUAD8) {
         // consecutive particles of the group with equal left node are summed
-        // in registers first (at most 4 * 2^24 per word), then added once
+        // in registers first (at most W 2^24 <= 2^27 per word), then added once
         unsigned key = 0xffffffffu, left = 0, right = 0;
         bool bad = false;
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
+        for (int k = 0; k < W; k++) {
             const Loc l = locate(xs[k]);
             const bool ok = valid && l.j <= (unsigned)c.ng;
             bad |= valid && !ok;
-            const unsigned W = fixed_weight(l.f);
+            const unsigned Wk = fixed_weight(l.f);
             if (ok && l.j == key) {
-                left += kFixOne - W;
-                right += W;
+                left += kFixOne - Wk;
+                right += Wk;
             } else if (ok) {
                 if (key != 0xffffffffu) {
                     tile_add(t, key, left);
                     tile_add(t, key + 1, right);
                 }
                 key = l.j;
-                left = kFixOne - W;
-                right = W;
+                left = kFixOne - Wk;
+                right = Wk;
             }
         }
         if (key != 0xffffffffu) {
@@ -229,8 +230,16 @@ __device__ __forceinline__ void deposit4(const Tile &t, const float4 &xx, bool v
         if (bad) atomicOr(err, kErrPosition);
     } else {
 #pragma unroll
-        for (int k = 0; k < 4; k++) deposit_one<VARIANT>(t, xs[k], valid, c, err, lane);
+        for (int k = 0; k < W; k++) deposit_one<VARIANT>(t, xs[k], valid, c, err, lane);
     }
+}
+
+// Deposit the 4 particles of a float4 group (valid per lane).
+template <int VARIANT>
+__device__ __forceinline__ void deposit4(const Tile &t, const float4 &xx, bool valid,
+                                         const PushConsts &c, unsigned *err, int lane) {
+    const float xs[4] = {xx.x, xx.y, xx.z, xx.w};
+    deposit_group<VARIANT, 4>(t, xs, valid, c, err, lane);
 }
 
 }  // namespace pic

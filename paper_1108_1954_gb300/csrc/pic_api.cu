@@ -30,8 +30,11 @@ bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
 bool is_variant(int v) {
     return v == PIC_DEPOSIT_ATOMIC || v == PIC_DEPOSIT_MATCH || v == PIC_DEPOSIT_QUAD ||
-           v == PIC_DEPOSIT_PAIR;
+           v == PIC_DEPOSIT_PAIR || v == PIC_DEPOSIT_QUAD8 || v == PIC_DEPOSIT_PAIR8;
 }
+
+// particles a thread takes per group: 8 for the 32-byte variants, else 4
+int group_width(int v) { return v == PIC_DEPOSIT_QUAD8 || v == PIC_DEPOSIT_PAIR8 ? 8 : 4; }
 
 }  // namespace
 
@@ -344,7 +347,9 @@ int push_grid(const pic_run *r, int variant, int block, int unroll, int bps_cap)
     if (bps < 1) return 0;
     if (bps_cap && bps_cap < bps) bps = bps_cap;
     long long want = (long long)r->sms * bps;
-    const long long units = r->p.precision == PIC_FP32_FIXED ? (r->p.npart + 3) / 4 : r->p.npart;
+    const int gw = group_width(variant);
+    const long long units = r->p.precision == PIC_FP32_FIXED ? (r->p.npart + gw - 1) / gw
+                                                             : r->p.npart;
     const long long per_block = (long long)block * unroll;
     const long long need = (units + per_block - 1) / per_block;
     if (want > need) want = need;
@@ -737,7 +742,7 @@ int pic_autotune(pic_run *run, int32_t reps, pic_tune_entry *results,
     if (nresults) *nresults = 0;
     if (run->p.precision != PIC_FP32_FIXED) return PIC_OK;
     static const int variants[] = {PIC_DEPOSIT_ATOMIC, PIC_DEPOSIT_MATCH, PIC_DEPOSIT_QUAD,
-                                   PIC_DEPOSIT_PAIR};
+                                   PIC_DEPOSIT_PAIR, PIC_DEPOSIT_QUAD8, PIC_DEPOSIT_PAIR8};
     static const int ngp_only[] = {kDepositNgp};
     static const int blocks[] = {128, 256, 512};
     static const int unrolls[] = {1, 2};

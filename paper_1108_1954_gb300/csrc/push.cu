@@ -165,6 +165,105 @@ __global__ void __launch_bounds__(512) pic_push_fixed_kernel(PushArgs a) {
     flush_tile(tile, a.rho_q, ng);
 }
 
+// ---- the fused push on 8-particle groups (QUAD8, PAIR8) ---------------------
+//
+// The same step, each thread taking 8 consecutive particles per group: one
+// 32-byte vector load (and store) per array, lanes of a warp on consecutive
+// groups (1 KB per warp and array, coalesced), and the deposit's runs of
+// equal cell merged over all 8 particles, which halves the shared-memory
+// atomics where neighbours share a cell (a sorted state, cold beams).
+struct F8 {
+    float v[8];
+};
+
+__device__ __forceinline__ F8 ld8(const float *p) {
+    F8 r;
+    asm volatile("ld.global.cs.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]), "=f"(r.v[4]),
+                   "=f"(r.v[5]), "=f"(r.v[6]), "=f"(r.v[7])
+                 : "l"(p));
+    return r;
+}
+
+__device__ __forceinline__ void st8(float *p, const F8 &r) {
+    asm volatile("st.global.cs.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p),
+                 "f"(r.v[0]), "f"(r.v[1]), "f"(r.v[2]), "f"(r.v[3]), "f"(r.v[4]), "f"(r.v[5]),
+                 "f"(r.v[6]), "f"(r.v[7])
+                 : "memory");
+}
+
+template <int VARIANT, bool PUSH, int U>
+__global__ void __launch_bounds__(512) pic_push_oct_kernel(PushArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ double red[64];
+    const PushConsts c = a.c;
+    const int ng = c.ng;
+    Tile tile;                                                       // 8 (ng + 2) B
+    tile.lo = reinterpret_cast<unsigned *>(smem_raw);
+    tile.hi = tile.lo + ng + 2;
+    float *sE = reinterpret_cast<float *>(smem_raw + 8 * (ng + 2));  // ng + 2
+    const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31;
+    for (int j = tid; j < ng + 2; j += bs) {
+        tile.lo[j] = 0u;
+        tile.hi[j] = 0u;
+        if (PUSH) sE[j] = a.E32[j == 0 ? ng - 1 : (j == ng + 1 ? 0 : j - 1)];
+    }
+    __syncthreads();
+
+    float ke = 0.0f, mom = 0.0f;
+    const long long n8 = a.n >> 3;
+    const long long span = (long long)bs * U;
+    const long long stride = (long long)gridDim.x * span;
+    F8 zero8;
+#pragma unroll
+    for (int k = 0; k < 8; k++) zero8.v[k] = 0.0f;
+    // no loads ahead: a group's 16 values per thread are its registers'
+    // worth, and three resident blocks hide the load latency instead
+    for (long long q0 = (long long)blockIdx.x * span; q0 < n8; q0 += stride) {
+        F8 cx[U], cv[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const long long q = q0 + u * bs + tid;
+            cx[u] = q < n8 ? ld8(a.x + 8 * q) : zero8;
+            cv[u] = (PUSH && q < n8) ? ld8(a.v + 8 * q) : zero8;
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const long long q = q0 + u * bs + tid;
+            const bool valid = q < n8;
+            F8 xx = cx[u], vv = cv[u];
+            if (PUSH && valid) {
+#pragma unroll
+                for (int k = 0; k < 8; k++) push_particle(xx.v[k], vv.v[k], sE, c, ke, mom);
+            }
+            deposit_group<VARIANT, 8>(tile, xx.v, valid, c, a.err, lane);
+            if (PUSH && valid) {
+                st8(a.x + 8 * q, xx);
+                st8(a.v + 8 * q, vv);
+            }
+        }
+    }
+    // The last N mod 8 particles: warp 0 of block 0, converged.
+    if (blockIdx.x == 0 && tid < 32) {
+        const long long i = n8 * 8 + lane;
+        const bool valid = i < a.n;
+        float xs = valid ? a.x[i] : 0.0f, vs = valid && PUSH ? a.v[i] : 0.0f;
+        if (PUSH && valid) push_particle(xs, vs, sE, c, ke, mom);
+        deposit_one<VARIANT>(tile, xs, valid, c, a.err, lane);
+        if (PUSH && valid) { a.x[i] = xs; a.v[i] = vs; }
+    }
+    if (PUSH) {
+        double dke = ke, dmom = mom;
+        __syncthreads();
+        block_sum2(dke, dmom, red);
+        if (tid == 0) {
+            a.partials[2 * blockIdx.x] = dke;
+            a.partials[2 * blockIdx.x + 1] = dmom;
+        }
+    }
+    flush_tile(tile, a.rho_q, ng);
+}
+
 // ---- float32 push with float32 atomic deposit (precision study) -------------
 
 template <bool PUSH>
@@ -314,8 +413,20 @@ FixedKernel pick_unroll(bool push, int unroll) {
     }
 }
 
+template <int V>
+FixedKernel pick_oct(bool push, int unroll) {
+    if (!push) return &pic_push_oct_kernel<V, false, 1>;
+    switch (unroll) {
+        case 1: return &pic_push_oct_kernel<V, true, 1>;
+        case 2: return &pic_push_oct_kernel<V, true, 2>;
+        default: return nullptr;
+    }
+}
+
 FixedKernel pick_fixed(int variant, bool push, int unroll) {
     switch (variant) {
+        case PIC_DEPOSIT_QUAD8: return pick_oct<PIC_DEPOSIT_QUAD8>(push, unroll);
+        case PIC_DEPOSIT_PAIR8: return pick_oct<PIC_DEPOSIT_PAIR8>(push, unroll);
         case PIC_DEPOSIT_ATOMIC: return pick_unroll<PIC_DEPOSIT_ATOMIC>(push, unroll);
         case PIC_DEPOSIT_MATCH: return pick_unroll<PIC_DEPOSIT_MATCH>(push, unroll);
         case PIC_DEPOSIT_QUAD: return pick_unroll<PIC_DEPOSIT_QUAD>(push, unroll);
@@ -343,7 +454,8 @@ cudaError_t push_prepare_attributes(int mode, int ng) {
     if (mode == PIC_FP32_FIXED) {
         const int unrolls[3] = {1, 2, 4};
         const int fixed_variants[] = {PIC_DEPOSIT_ATOMIC, PIC_DEPOSIT_MATCH, PIC_DEPOSIT_QUAD,
-                                      PIC_DEPOSIT_PAIR, kDepositNgp};
+                                      PIC_DEPOSIT_PAIR, PIC_DEPOSIT_QUAD8, PIC_DEPOSIT_PAIR8,
+                                      kDepositNgp};
         for (int v : fixed_variants)
             for (int p = 0; p < 2; p++)
                 for (int u : unrolls) {

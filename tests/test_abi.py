@@ -52,7 +52,7 @@ def test_workspace_size_scales_with_particles(pic):
     dict(dt=0.0), dict(length=float("nan")), dict(length=-1.0),
     dict(rho_ion=0.0), dict(block_size=33), dict(block_size=2048),
     dict(block_size=1024), dict(unroll=3),
-    dict(deposit_variant=9), dict(deposit_variant=3), dict(deposit_variant=4),
+    dict(deposit_variant=10), dict(deposit_variant=3), dict(deposit_variant=4),
     dict(deposit_variant=7), dict(precision=7), dict(sort_interval=-1),
     dict(npart=1 << 33)])
 def test_invalid_parameters_rejected(pic, bad):

@@ -125,19 +125,42 @@ def test_deposit_variants_and_shapes_identical(variant, block, unroll):
     assert np.array_equal(xa, xb) and np.array_equal(va, vb)
 
 
+@pytest.mark.parametrize("variant", [8, 9])
+@pytest.mark.parametrize("block", [64, 256, 512])
+@pytest.mark.parametrize("unroll", [1, 2])
+def test_eight_particle_groups_identical(variant, block, unroll):
+    # the 32-byte group variants give the ATOMIC kernel's particles and
+    # integers bit for bit, with the N mod 8 tail
+    n, ng = 70005, 512
+    x, v = W.two_stream(n, L4PI, 0.2, 0.01, 3)
+    x32, v32 = W.to_f32_state(x, v, L4PI)
+    ref = make_run(n, ng, L4PI, deposit_variant=1, block_size=256)
+    ref.init(x32, v32)
+    ref.step_n(3)
+    run = make_run(n, ng, L4PI, deposit_variant=variant, block_size=block, unroll=unroll)
+    run.init(x32, v32)
+    run.step_n(3)
+    assert np.array_equal(run.get_field()["rho_q"], ref.get_field()["rho_q"])
+    assert np.array_equal(run.get_cells()[0], ref.get_cells()[0])
+    assert np.array_equal(run.get_cells()[1], ref.get_cells()[1])
+    with pytest.raises(pic.PicError):
+        run.set_launch(variant, block, 4)           # no 4-group build of these
+
+
 def test_all_particles_in_one_cell():
     # every particle in one cell: a block's low words wrap many times and the
     # carries into the high words must all be counted
     n, ng, L = 300001, 64, 64.0
     x32 = np.full(n, 10.3, dtype=np.float32)
     v32 = np.zeros(n, dtype=np.float32)
-    for variant in (1, 2, 5, 6):
+    for variant in (1, 2, 5, 6, 8, 9):
         run = make_run(n, ng, L, deposit_variant=variant, block_size=256, blocks_per_sm=1)
         run.init(x32, v32)
         assert np.array_equal(run.get_field()["rho_q"], O.deposit_fixed(ng, run.get_cells()[0]))
 
 
-@pytest.mark.parametrize("variant,block,unroll", [(1, 512, 1), (5, 64, 4), (2, 256, 2)])
+@pytest.mark.parametrize("variant,block,unroll", [(1, 512, 1), (5, 64, 4), (2, 256, 2),
+                                                  (8, 512, 1), (9, 256, 2)])
 def test_one_node_of_a_tile_wraps_many_times(variant, block, unroll):
     # 2^24 particles at one position, one block per SM: a block adds ~110,000
     # weights of about 2^24 to each of two nodes of its tile, so each node's
@@ -294,7 +317,8 @@ def test_ragged_sizes_identical_across_variants(n, ng):
     ref.init(x32, v32)
     ref.step_n(9)
     xb, vb = ref.get_state()
-    for variant, block, unroll in ((5, 512, 1), (6, 512, 2), (2, 128, 4)):
+    for variant, block, unroll in ((5, 512, 1), (6, 512, 2), (2, 128, 4), (8, 512, 1),
+                                   (9, 256, 2), (8, 128, 2)):
         run = make_run(n, ng, L4PI, deposit_variant=variant, block_size=block,
                        unroll=unroll, sort_interval=4)
         run.init(x32, v32)
