@@ -79,6 +79,10 @@ def parse():
     ap.add_argument("--only-batched", action="store_true",
                     help="run only the batched-ensemble section (profiling)")
     ap.add_argument("--no-tune-batched", action="store_true")
+    ap.add_argument("--pool-variant", type=int, default=1 + 16,
+                    help="the pool's deposit variant (+16: 64-register build) when not tuned")
+    ap.add_argument("--pool-cluster", type=int, default=8)
+    ap.add_argument("--pool-block", type=int, default=256)
     ap.add_argument("--only-precision", action="store_true",
                     help="run only the precision study (config 4)")
     ap.add_argument("--only-variant-scan", action="store_true",
@@ -404,8 +408,9 @@ def tune_pool(states, steps, history):
     """Autotuner of the batched launch, over the deposit variant and build,
     the cluster size, the block size (the tile shape) and the sort interval.
     The whole ensemble is admitted once; each (variant, cluster, block) is
-    timed over `steps` steps (after `steps` untimed ones) on the same
-    resident runs, the shape changed with pic_pool_configure.  Then, with the
+    timed over `steps` steps (after one untimed step) in each of three
+    rounds, on the same resident runs, the shape changed with
+    pic_pool_configure and the order shuffled per round.  Then, with the
     fastest shape, the ensemble is admitted again for each sort interval S
     and timed over 40 steps (after 10), long enough to include the sorts of
     every S tried.  Returns the fastest (variant, cluster, block, S) and the
@@ -428,23 +433,36 @@ def tune_pool(states, steps, history):
         pool.sync()
         return pool
 
+    # The resident runs evolve while the shapes are timed (cold beams early,
+    # mixed later), and the shapes differ most early on, so each shape is
+    # timed in several short windows spread over the first few hundred
+    # steps, the order shuffled every round.
+    import numpy as np
     pool = admit_all(0)
-    table = []
-    for variant in (1, 2, 5, 6, 1 + 16, 2 + 16, 5 + 16, 6 + 16):
+    shapes = []
+    for variant in (1, 5, 6, 1 + 16, 5 + 16, 6 + 16):
         for cluster in (4, 8):
             for block in (256, 512):
                 try:
                     pool.configure(variant, cluster, block)
                 except pic.PicError:
                     continue
-                pool.advance(steps)
-                e0.record(pool.stream)
-                pool.advance(steps)
-                e1.record(pool.stream)
-                pool.sync()
-                table.append(((variant, cluster, block), e0.elapsed_time(e1)))
+                shapes.append((variant, cluster, block))
+    total = {sh: 0.0 for sh in shapes}
+    rng = np.random.default_rng(7)
+    rounds = 3
+    for _ in range(rounds):
+        for i in rng.permutation(len(shapes)):
+            sh = shapes[i]
+            pool.configure(*sh)
+            pool.advance(1)
+            e0.record(pool.stream)
+            pool.advance(steps)
+            e1.record(pool.stream)
+            pool.sync()
+            total[sh] += e0.elapsed_time(e1)
     pool.close()
-    table.sort(key=lambda t: t[1])
+    table = sorted(((sh, t / rounds) for sh, t in total.items()), key=lambda t: t[1])
     shape = table[0][0]
     sort_table = []
     for S in (0, 10, 20, 40):
@@ -470,9 +488,9 @@ def time_batched(args):
     states = ensemble_states(args.batched_runs, 3)
     total_particles = sum(p.npart for p, _, _ in states)
     if args.no_tune_batched:
-        best, table, sort_table = (1 + 16, 8, 256, 0), [], []
+        best, table, sort_table = (args.pool_variant, args.pool_cluster, args.pool_block, 0), [], []
     else:
-        best, table, sort_table = tune_pool(states, 10, H)
+        best, table, sort_table = tune_pool(states, 4, H)
     S = best[3]
     sorted_states = [(pic.Params(npart=p.npart, ncell=p.ncell, length=p.length, dt=p.dt,
                                  sort_interval=S), x, v) for p, x, v in states]

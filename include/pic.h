@@ -414,9 +414,10 @@ typedef struct pic_pool_config {
     int32_t max_slots;     /* runs held at once (>= 1)                         */
     int32_t ncell_max;     /* largest NG admitted (<= PIC_NCELL_MAX)            */
     int32_t history;       /* diagnostics rows kept per run (>= 1)              */
-    int32_t variant;       /* PIC_DEPOSIT_ATOMIC | _MATCH | _QUAD (0 = MATCH);
-                              + 16: kernel built for two blocks per SM
-                              (64 registers) instead of one                  */
+    int32_t variant;       /* PIC_DEPOSIT_ATOMIC | _MATCH | _QUAD | _PAIR
+                              (0 = MATCH); + 16: kernel built for two
+                              512-thread blocks per SM (64 registers)
+                              instead of one                                 */
     int32_t cluster;       /* blocks per cluster: 1, 2, 4, 8 (0 = 8)            */
     int32_t block;         /* threads per block: 128 .. 512 (0 = 256); the
                               shape needs ceil(ncell_max / cluster) <= block   */

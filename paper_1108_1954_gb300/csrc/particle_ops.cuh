@@ -12,6 +12,44 @@ namespace pic {
 
 using u64 = unsigned long long;
 
+// 8 consecutive float32 values moved by one 32-byte vector load or store
+// (the QUAD8 and PAIR8 variants; the address 32-byte aligned).  .cs:
+// streamed (the single run's arrays pass once per step); .cg: cached in L2
+// only (the batched kernel's runs).
+struct F8 {
+    float v[8];
+};
+
+template <bool CG = false>
+__device__ __forceinline__ F8 ld8(const float *p) {
+    F8 r;
+    if (CG)
+        asm volatile("ld.global.cg.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]), "=f"(r.v[4]),
+                       "=f"(r.v[5]), "=f"(r.v[6]), "=f"(r.v[7])
+                     : "l"(p));
+    else
+        asm volatile("ld.global.cs.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]), "=f"(r.v[4]),
+                       "=f"(r.v[5]), "=f"(r.v[6]), "=f"(r.v[7])
+                     : "l"(p));
+    return r;
+}
+
+template <bool CG = false>
+__device__ __forceinline__ void st8(float *p, const F8 &r) {
+    if (CG)
+        asm volatile("st.global.cg.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p),
+                     "f"(r.v[0]), "f"(r.v[1]), "f"(r.v[2]), "f"(r.v[3]), "f"(r.v[4]),
+                     "f"(r.v[5]), "f"(r.v[6]), "f"(r.v[7])
+                     : "memory");
+    else
+        asm volatile("st.global.cs.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p),
+                     "f"(r.v[0]), "f"(r.v[1]), "f"(r.v[2]), "f"(r.v[3]), "f"(r.v[4]),
+                     "f"(r.v[5]), "f"(r.v[6]), "f"(r.v[7])
+                     : "memory");
+}
+
 // Cell location of a float32 cell coordinate u (the fixed-point recipe):
 //   s = u - 1/2, fl = floor(s), f = s - fl   (float ops, round to nearest)
 // floor(s) is formed as (s + 1.5*2^23 rounded down) - 1.5*2^23, which equals

@@ -172,26 +172,6 @@ __global__ void __launch_bounds__(512) pic_push_fixed_kernel(PushArgs a) {
 // groups (1 KB per warp and array, coalesced), and the deposit's runs of
 // equal cell merged over all 8 particles, which halves the shared-memory
 // atomics where neighbours share a cell (a sorted state, cold beams).
-struct F8 {
-    float v[8];
-};
-
-__device__ __forceinline__ F8 ld8(const float *p) {
-    F8 r;
-    asm volatile("ld.global.cs.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                 : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]), "=f"(r.v[4]),
-                   "=f"(r.v[5]), "=f"(r.v[6]), "=f"(r.v[7])
-                 : "l"(p));
-    return r;
-}
-
-__device__ __forceinline__ void st8(float *p, const F8 &r) {
-    asm volatile("st.global.cs.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p),
-                 "f"(r.v[0]), "f"(r.v[1]), "f"(r.v[2]), "f"(r.v[3]), "f"(r.v[4]), "f"(r.v[5]),
-                 "f"(r.v[6]), "f"(r.v[7])
-                 : "memory");
-}
-
 template <int VARIANT, bool PUSH, int U>
 __global__ void __launch_bounds__(512) pic_push_oct_kernel(PushArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
