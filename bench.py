@@ -186,13 +186,21 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def recorded_traffic():
+def push_kernel_name(variant):
+    """The fused push kernel a deposit variant runs in."""
+    return "pic_push_oct_kernel" if variant in (8, 9) else "pic_push_fixed_kernel"
+
+
+def recorded_traffic(variant=None):
     """DRAM bytes per launch of the fused push from the committed ncu summary,
-    if the kernel source is unchanged since the capture."""
+    if it was captured for this deposit variant and the kernel source is
+    unchanged since the capture."""
     path = os.path.join(ROOT, "profiles", "push_fixed_traffic.json")
     try:
         rec = json.load(open(path))
     except (OSError, ValueError):
+        return None
+    if variant is not None and rec.get("variant") != variant:
         return None
     m = hashlib.sha256()
     for f in rec.get("source_files", []):
@@ -997,8 +1005,8 @@ def main():
                               "blocks_per_sm": res["blocks_per_sm"]},
                    "sort_interval_tuner": res["sort_tune"]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": recorded_traffic(),
-                     "kernel": "pic_push_fixed_kernel", "peak_source": src,
+                     "frac": achieved / peak, "traffic": recorded_traffic(res["variant"]),
+                     "kernel": push_kernel_name(res["variant"]), "peak_source": src,
                      "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP,
                      "push_ms_avg": push_avg_s * 1e3,
                      "push_ms_by_window": [round(statistics.mean(res["push_ms"][i:i + 100]), 4)
