@@ -977,15 +977,15 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu:
         nt = host_threads()
-        c1 = time_oracle(w, x32, v32, budget_s=10.0)
-        c = time_oracle(w, x32, v32, budget_s=10.0, threads=nt) if nt > 1 else c1
+        one = time_oracle(w, x32, v32, budget_s=10.0)
+        c = time_oracle(w, x32, v32, budget_s=10.0, threads=nt) if nt > 1 else one
         cpu = {"value": c["value"], "unit": "particle-steps/s", "cores": nt, "kind": "oracle",
                "cpu": cpu_model(),
                "sample": "FP64 oracle on the full %d-particle state, first %d steps (%.1f s) on "
                          "%d host threads" % (c["npart"], c["steps"], c["seconds"], nt),
-               "value_1core": c1["value"],
+               "value_1core": one["value"],
                "sample_1core": "the same on one thread: first %d steps (%.1f s)"
-                               % (c1["steps"], c1["seconds"])}
+                               % (one["steps"], one["seconds"])}
     if rank != 0:
         torch.distributed.destroy_process_group()
         return
