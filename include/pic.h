@@ -343,10 +343,15 @@ typedef struct pic_tune_entry {
 } pic_tune_entry;
 
 /* Autotune the fused push (PIC_FP32_FIXED): time every candidate shape
- * (deposit variant x block size x unroll) for `reps` pushes on a copy of the
- * current particles (the sort buffers and a scratch density accumulator; the
- * run's state is untouched) and, when the run sorts, on a freshly sorted copy
- * too; adopt the one with the smallest mean time.  Writes up to
+ * (deposit variant x block size x unroll) on a copy of the current particles
+ * (the sort buffers and a scratch density accumulator; the run's state is
+ * untouched), pushed with the current field: `reps` pushes of the copy as it
+ * is, or, when the run sorts every S steps, min(S, 64) pushes of a freshly
+ * sorted copy (one sort period); adopt the one with the smallest mean push
+ * time.  The order of a sorting run settles after its first sorts (within a
+ * cell, particles keep the order of the cells they came from, so of their
+ * velocities), and the fastest shape changes with it: tune after those.
+ * Writes up to
  * max_results entries to results (may be NULL) and their count to *nresults.
  * Synchronises.  PIC_ESTATE before pic_init or between pic_push and
  * pic_solve_field. */

@@ -748,17 +748,26 @@ int pic_autotune(pic_run *run, int32_t reps, pic_tune_entry *results,
     static const int unrolls[] = {1, 2};
     const size_t bytes = (size_t)run->p.npart * run->elem();
     const int c = run->cur;
-    cudaEvent_t e0, e1;
-    PIC_CUDA(cudaEventCreate(&e0));
-    PIC_CUDA(cudaEventCreate(&e1));
+    cudaEvent_t ev[128];
+    int made = 0;
+    for (; made < 128; made++) {
+        const cudaError_t ec = cudaEventCreate(&ev[made]);
+        if (ec != cudaSuccess) {
+            for (int i = 0; i < made; i++) cudaEventDestroy(ev[i]);
+            return cuda_fail(ec);
+        }
+    }
     float best = 1e30f;
     int bv = run->variant, bb = run->block, bu = run->unroll, bg = run->grid, count = 0;
     int rc = PIC_OK;
-    // With sorting on, the particle order cycles between freshly sorted (many
-    // lanes of a warp in one cell) and drifted apart; each candidate is timed
-    // on a copy of the current order and on a freshly sorted copy, and the sum
-    // is minimised.
-    const int phases = run->p.sort_interval > 0 ? 2 : 1;
+    // A run that sorts every S steps spends each period drifting away from a
+    // freshly sorted order (many lanes of a warp in one cell right after the
+    // sort, spread apart later), so a candidate is timed over one period:
+    // the copy is sorted, then pushed min(S, 64) times with the current
+    // field, and the mean is minimised.  Without sorting, `reps` pushes of a
+    // copy of the current order (which drifts as it is pushed).
+    const int S = run->p.sort_interval;
+    const int nrep = S > 0 ? (S < 64 ? S : 64) : (reps < 64 ? reps : 64);
     const bool ngp = run->p.shape == PIC_SHAPE_NGP;
     const int *vlist = ngp ? ngp_only : variants;
     const int nv = ngp ? 1 : (int)(sizeof(variants) / sizeof(variants[0]));
@@ -777,34 +786,27 @@ int pic_autotune(pic_run *run, int32_t reps, pic_tune_entry *results,
                 a.partials = run->at<double>(run->lay.partials);
                 a.err = &run->dev()->err;
                 a.c = run->pc;
-                float total = 0.0f;
-                for (int ph = 0; ph < phases; ph++) {
-                    cudaError_t e;
-                    if (ph == 0) {
-                        e = cudaMemcpyAsync(a.x, run->xs(c), bytes, cudaMemcpyDeviceToDevice, run->stream);
-                        if (e == cudaSuccess)
-                            e = cudaMemcpyAsync(a.v, run->vs(c), bytes, cudaMemcpyDeviceToDevice, run->stream);
-                    } else {
-                        e = enqueue_sort_into(run, c, run->stream);
-                    }
-                    if (e == cudaSuccess) e = launch_push_fixed(a, g, b, v, u, true, run->stream);  // warm
-                    float times[64];
-                    const int nrep = reps < 64 ? reps : 64;
-                    for (int i = 0; i < nrep && e == cudaSuccess; i++) {
-                        e = cudaEventRecord(e0, run->stream);
-                        if (e == cudaSuccess) e = launch_push_fixed(a, g, b, v, u, true, run->stream);
-                        if (e == cudaSuccess) e = cudaEventRecord(e1, run->stream);
-                        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-                        if (e == cudaSuccess) e = cudaEventElapsedTime(&times[i], e0, e1);
-                    }
-                    if (e != cudaSuccess) { rc = cuda_fail(e); goto done; }
-                    // the repeats push the copy onward (its order drifts),
-                    // so their mean is the figure of merit
-                    float sum = 0.0f;
-                    for (int i = 0; i < nrep; i++) sum += times[i];
-                    total += sum / (float)nrep;
+                cudaError_t e = cudaMemcpyAsync(a.x, run->xs(c), bytes, cudaMemcpyDeviceToDevice,
+                                                run->stream);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(a.v, run->vs(c), bytes, cudaMemcpyDeviceToDevice, run->stream);
+                if (e == cudaSuccess) e = launch_push_fixed(a, g, b, v, u, true, run->stream);  // warm
+                if (e == cudaSuccess && S > 0) e = enqueue_sort_into(run, c, run->stream);
+                // the pushes go back to back, as in a run, and are read after
+                for (int i = 0; i < nrep && e == cudaSuccess; i++) {
+                    e = cudaEventRecord(ev[2 * i], run->stream);
+                    if (e == cudaSuccess) e = launch_push_fixed(a, g, b, v, u, true, run->stream);
+                    if (e == cudaSuccess) e = cudaEventRecord(ev[2 * i + 1], run->stream);
                 }
-                const float med = total / (float)phases;
+                if (e == cudaSuccess) e = cudaStreamSynchronize(run->stream);
+                float total = 0.0f;
+                for (int i = 0; i < nrep && e == cudaSuccess; i++) {
+                    float ms = 0.0f;
+                    e = cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+                    total += ms;
+                }
+                if (e != cudaSuccess) { rc = cuda_fail(e); goto done; }
+                const float med = total / (float)nrep;
                 if (results && count < max_results) results[count] = pic_tune_entry{v, b, u, g, med};
                 count++;
                 if (med < best) { best = med; bv = v; bb = b; bu = u; bg = g; }
@@ -817,8 +819,7 @@ int pic_autotune(pic_run *run, int32_t reps, pic_tune_entry *results,
     destroy_graphs(run);
     if (nresults) *nresults = count < max_results || !results ? count : max_results;
 done:
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    for (int i = 0; i < made; i++) cudaEventDestroy(ev[i]);
     if (rc) return rc;
     PIC_CUDA(cudaMemsetAsync(run->ws + run->lay.tune_rho, 0, (size_t)run->p.ncell * 8, run->stream));
     return read_error_word(run);

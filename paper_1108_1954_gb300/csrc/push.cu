@@ -474,7 +474,11 @@ int push_max_blocks_per_sm(int mode, int variant, int unroll, int block, int ng)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, &pic_push_f32atomic_kernel<true>, block, smem);
     else
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, &pic_push_f64_kernel<true>, block, smem);
-    return e == cudaSuccess ? nb : 0;
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();     // do not leave the error for a later launch check
+        return 0;
+    }
+    return nb;
 }
 
 cudaError_t launch_push_fixed(const PushArgs &a, int grid, int block, int variant,
