@@ -191,16 +191,21 @@ def push_kernel_name(variant):
     return "pic_push_oct_kernel" if variant in (8, 9) else "pic_push_fixed_kernel"
 
 
-def recorded_traffic(variant=None):
-    """DRAM bytes per launch of the fused push from the committed ncu summary,
-    if it was captured for this deposit variant and the kernel source is
-    unchanged since the capture."""
+def recorded_traffic(variant=None, unroll=None):
+    """DRAM bytes per launch of the fused push from the committed ncu summary:
+    the entry captured for this deposit variant and unroll (the first entry
+    when none is given), if the kernel source is unchanged since the
+    capture."""
     path = os.path.join(ROOT, "profiles", "push_fixed_traffic.json")
     try:
         rec = json.load(open(path))
     except (OSError, ValueError):
         return None
-    if variant is not None and rec.get("variant") != variant:
+    entries = rec.get("launches", [])
+    if variant is not None:
+        entries = [e for e in entries if e.get("variant") == variant and
+                   (unroll is None or e.get("unroll") == unroll)]
+    if not entries:
         return None
     m = hashlib.sha256()
     for f in rec.get("source_files", []):
@@ -210,7 +215,7 @@ def recorded_traffic(variant=None):
             return None
     if rec.get("source_sha256") != m.hexdigest():
         return None
-    return rec.get("bytes_per_launch_c2")
+    return entries[0].get("bytes_per_launch_c2")
 
 
 def time_ours(args, w, x32, v32):
@@ -1011,7 +1016,7 @@ def main():
                               "blocks_per_sm": res["blocks_per_sm"]},
                    "sort_interval_tuner": res["sort_tune"]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": recorded_traffic(res["variant"]),
+                     "frac": achieved / peak, "traffic": recorded_traffic(res["variant"], res["unroll"]),
                      "kernel": push_kernel_name(res["variant"]), "peak_source": src,
                      "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP,
                      "push_ms_avg": push_avg_s * 1e3,

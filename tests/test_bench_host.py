@@ -54,7 +54,10 @@ def test_recorded_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
     rec["source_sha256"] = m.hexdigest()
     (tmp_path / "profiles" / "push_fixed_traffic.json").write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.recorded_traffic() == rec["bytes_per_launch_c2"]
+    first = rec["launches"][0]
+    assert bench.recorded_traffic() == first["bytes_per_launch_c2"]
+    assert bench.recorded_traffic(first["variant"], first["unroll"]) == first["bytes_per_launch_c2"]
+    assert bench.recorded_traffic(1, 1) is None               # no capture of that shape
     with open(tmp_path / rec["source_files"][0], "a") as fh:
         fh.write("\n// changed\n")
     assert bench.recorded_traffic() is None
