@@ -151,6 +151,8 @@ struct pic_run {
     int device = 0, sms = 0;
     cudaStream_t stream = nullptr;   // the caller's
     cudaStream_t cap = nullptr;      // private stream for graph capture
+    cudaStream_t aux = nullptr;      // private stream: the second host copy of a load or read-back
+    cudaEvent_t fork = nullptr, join = nullptr;
     unsigned char *ws = nullptr;
     int cur = 0;                     // which x/v buffer holds the state
     int grid = 0, block = 0, variant = 0, unroll = 1;
@@ -358,6 +360,18 @@ int push_grid(const pic_run *r, int variant, int block, int unroll, int bps_cap)
     return (int)want;
 }
 
+// Work on the private stream after everything enqueued on the run's stream
+// so far (fork), and the run's stream after that work (join).
+cudaError_t fork_aux(pic_run *r) {
+    cudaError_t e = cudaEventRecord(r->fork, r->stream);
+    return e == cudaSuccess ? cudaStreamWaitEvent(r->aux, r->fork, 0) : e;
+}
+
+cudaError_t join_aux(pic_run *r) {
+    cudaError_t e = cudaEventRecord(r->join, r->aux);
+    return e == cudaSuccess ? cudaStreamWaitEvent(r->stream, r->join, 0) : e;
+}
+
 int read_error_word(pic_run *r) {
     unsigned err = 0;
     PIC_CUDA(cudaMemcpyAsync(&err, &r->dev()->err, sizeof(err), cudaMemcpyDeviceToHost, r->stream));
@@ -371,7 +385,7 @@ enum class Units { kPhysical, kCells };
 
 // With x, v in buffer 0: check (and, in the float32 modes, convert to cell
 // coordinates) the positions, reset the run, deposit and solve: E^step ready.
-int prepare_loaded(pic_run *r, int64_t step, Units units) {
+int prepare_loaded(pic_run *r, int64_t step, Units units, bool aux_copy = false) {
     DevScalars ds{};
     ds.step = step;
     PIC_CUDA(cudaMemcpyAsync(r->dev(), &ds, sizeof(ds), cudaMemcpyHostToDevice, r->stream));
@@ -390,6 +404,7 @@ int prepare_loaded(pic_run *r, int64_t step, Units units) {
     PIC_CUDA(cudaMemsetAsync(r->ws + r->lay.hist, 0xFF, (size_t)r->lay.hist_len * sizeof(pic_diag_row), r->stream));
     PIC_CUDA(enqueue_push(r, r->stream, false));
     PIC_CUDA(enqueue_solve(r, r->stream, false));
+    if (aux_copy) PIC_CUDA(join_aux(r));
     PIC_CUDA(cudaStreamSynchronize(r->stream));
     r->step = step;
     r->pending_push = false;
@@ -401,13 +416,17 @@ int prepare_loaded(pic_run *r, int64_t step, Units units) {
 // Upload a state, deposit it and solve: E^step ready.
 // The positions are range-checked (and converted) on the device after the
 // upload (a host loop over N positions cost more than the whole upload).
+// The positions go up first; the velocities follow on the private stream
+// while the positions are converted and deposited and the field is solved
+// (none of which reads v), so that work hides under the second copy.
 int load_state(pic_run *r, const void *x, const void *v, int64_t step, Units units) {
     if (!x || !v) return PIC_EINVAL;
     const size_t bytes = (size_t)r->p.npart * r->elem();
     r->cur = 0;
     PIC_CUDA(cudaMemcpyAsync(r->xs(0), x, bytes, cudaMemcpyHostToDevice, r->stream));
-    PIC_CUDA(cudaMemcpyAsync(r->vs(0), v, bytes, cudaMemcpyHostToDevice, r->stream));
-    return prepare_loaded(r, step, units);
+    PIC_CUDA(fork_aux(r));
+    PIC_CUDA(cudaMemcpyAsync(r->vs(0), v, bytes, cudaMemcpyHostToDevice, r->aux));
+    return prepare_loaded(r, step, units, true);
 }
 
 }  // namespace
@@ -459,7 +478,10 @@ int pic_create(const pic_params *p, void *workspace, size_t workspace_bytes,
     if (e == cudaSuccess) e = sort_prepare_attributes(p->ncell);
     if (e == cudaSuccess) e = solve_prepare_attributes();
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&r->cap, cudaStreamNonBlocking);
-    if (e != cudaSuccess) { delete r; return cuda_fail(e); }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&r->aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->join, cudaEventDisableTiming);
+    if (e != cudaSuccess) { pic_destroy(r); return cuda_fail(e); }
 
     // float32 constants of the push in cell units (u = x NG/L)
     r->pc.ng = p->ncell;
@@ -488,6 +510,9 @@ void pic_destroy(pic_run *run) {
     if (!run) return;
     destroy_graphs(run);
     if (run->cap) cudaStreamDestroy(run->cap);
+    if (run->aux) cudaStreamDestroy(run->aux);
+    if (run->fork) cudaEventDestroy(run->fork);
+    if (run->join) cudaEventDestroy(run->join);
     delete run;
 }
 
@@ -631,6 +656,12 @@ int pic_get_state(pic_run *run, void *x, void *v) {
     if (!run) return PIC_EINVAL;
     if (!run->ready) return PIC_ESTATE;
     const size_t bytes = (size_t)run->p.npart * run->elem();
+    // the velocities go down on the private stream while the positions are
+    // converted, then the positions follow
+    if (v) {
+        PIC_CUDA(fork_aux(run));
+        PIC_CUDA(cudaMemcpyAsync(v, run->vs(run->cur), bytes, cudaMemcpyDeviceToHost, run->aux));
+    }
     if (x) {
         const void *src = run->xs(run->cur);
         if (run->p.precision != PIC_FP64) {
@@ -642,7 +673,7 @@ int pic_get_state(pic_run *run, void *x, void *v) {
         }
         PIC_CUDA(cudaMemcpyAsync(x, src, bytes, cudaMemcpyDeviceToHost, run->stream));
     }
-    if (v) PIC_CUDA(cudaMemcpyAsync(v, run->vs(run->cur), bytes, cudaMemcpyDeviceToHost, run->stream));
+    if (v) PIC_CUDA(join_aux(run));
     PIC_CUDA(cudaStreamSynchronize(run->stream));
     return read_error_word(run);
 }
