@@ -359,14 +359,36 @@ class Run:
         _check(_lib.pic_set_launch(self._h, int(variant), int(block), int(unroll),
                                    int(blocks_per_sm)), "pic_set_launch")
 
-    def autotune(self, reps: int = 5) -> np.ndarray:
+    def autotune(self, reps: int = 5, cache: str | None = None) -> np.ndarray:
         """Time the candidate push shapes on a copy of the state and adopt
-        the fastest; returns the timings."""
+        the fastest; returns the timings.  With `cache` (a file path), a
+        shape already adopted for a run of this kind on this GPU model is
+        taken from the file without timing (an empty table is returned), and
+        a newly adopted shape is added to it."""
+        k = None
+        if cache is not None:
+            import torch
+            from . import tune_cache
+            k = tune_cache.key(torch.cuda.get_device_name(self.device), self.p.npart,
+                               self.p.ncell, self.p.sort_interval, self.p.precision,
+                               self.p.shape)
+            hit = tune_cache.lookup(cache, k)
+            if hit is not None:
+                self.set_launch(hit["variant"], hit["block"], hit["unroll"])
+                return np.zeros(0, dtype=TUNE_DTYPE)
         out = np.zeros(64, dtype=TUNE_DTYPE)
         n = C.c_int32(0)
         _check(_lib.pic_autotune(self._h, int(reps), _VP(out.ctypes.data), 64, C.byref(n)),
                "pic_autotune")
-        return out[:n.value]
+        table = out[:n.value]
+        if k is not None and len(table):
+            from . import tune_cache
+            _, block, variant, unroll = self.launch_shape()
+            best = table[(table["variant"] == variant) & (table["block"] == block) &
+                         (table["unroll"] == unroll)]
+            tune_cache.store(cache, k, variant, block, unroll,
+                             float(best["ms"][0]) if len(best) else float("nan"))
+        return table
 
     def set_shard(self, npart_total: int):
         """This run holds one rank's particles of a plasma of npart_total."""

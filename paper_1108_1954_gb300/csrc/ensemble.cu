@@ -377,6 +377,7 @@ extern "C" {
 
 int pic_pool_admit(pic_pool *pool, const pic_params *p, const void *x0, const void *v0,
                    int64_t steps, int32_t *slot) {
+    pic::TraceRange trace_("pic_pool_admit");
     if (!pool || !p || !x0 || !v0 || !slot || steps < 0) return PIC_EINVAL;
     *slot = -1;
     int rc = check_admit(pool, p);
@@ -402,6 +403,7 @@ int pic_pool_admit(pic_pool *pool, const pic_params *p, const void *x0, const vo
 
 int pic_pool_admit_loaded(pic_pool *pool, const pic_params *p, const pic_loading *ld,
                           int64_t steps, int32_t *slot) {
+    pic::TraceRange trace_("pic_pool_admit_loaded");
     if (!pool || !p || !ld || !slot || steps < 0) return PIC_EINVAL;
     *slot = -1;
     int rc = check_admit(pool, p);
@@ -424,6 +426,7 @@ int pic_pool_admit_loaded(pic_pool *pool, const pic_params *p, const pic_loading
 }
 
 int pic_pool_advance(pic_pool *pool, int64_t k, int32_t *active) {
+    pic::TraceRange trace_("pic_pool_advance");
     if (!pool || k < 0) return PIC_EINVAL;
     if (active) *active = 0;
     std::vector<int> order;
@@ -485,6 +488,7 @@ int pic_pool_step_count(const pic_pool *pool, int32_t slot, int64_t *step) {
 }
 
 int pic_pool_get_cells(pic_pool *pool, int32_t slot, float *u, float *v) {
+    pic::TraceRange trace_("pic_pool_get_cells");
     if (!slot_ok(pool, slot)) return PIC_EINVAL;
     const pic_pool::Slot &sl = pool->slots[slot];
     if (sl.needs_init) return PIC_ESTATE;
@@ -495,6 +499,7 @@ int pic_pool_get_cells(pic_pool *pool, int32_t slot, float *u, float *v) {
 }
 
 int pic_pool_get_state(pic_pool *pool, int32_t slot, void *x, void *v) {
+    pic::TraceRange trace_("pic_pool_get_state");
     int rc = pic_pool_get_cells(pool, slot, (float *)x, (float *)v);
     if (rc || !x) return rc;
     // cell coordinates to physical positions on the host, with the same two
@@ -512,6 +517,7 @@ int pic_pool_get_state(pic_pool *pool, int32_t slot, void *x, void *v) {
 
 int pic_pool_get_field(pic_pool *pool, int32_t slot, double *rho, double *phi, double *E,
                        int64_t *rho_q) {
+    pic::TraceRange trace_("pic_pool_get_field");
     if (!slot_ok(pool, slot)) return PIC_EINVAL;
     const pic_pool::Slot &sl = pool->slots[slot];
     if (sl.needs_init) return PIC_ESTATE;
@@ -526,6 +532,7 @@ int pic_pool_get_field(pic_pool *pool, int32_t slot, double *rho, double *phi, d
 
 int pic_pool_diagnostics(pic_pool *pool, int32_t slot, int64_t first, int32_t count,
                          pic_diag_row *rows) {
+    pic::TraceRange trace_("pic_pool_diagnostics");
     if (!slot_ok(pool, slot) || !rows || count < 0 || first < 0) return PIC_EINVAL;
     const pic_pool::Slot &sl = pool->slots[slot];
     const int64_t H = pool->cfg.history;

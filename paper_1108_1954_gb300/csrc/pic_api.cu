@@ -517,11 +517,13 @@ void pic_destroy(pic_run *run) {
 }
 
 int pic_init(pic_run *run, const void *x0, const void *v0) {
+    pic::TraceRange trace_("pic_init");
     if (!run) return PIC_EINVAL;
     return load_state(run, x0, v0, 0, Units::kPhysical);
 }
 
 int pic_init_loaded(pic_run *run, const pic_loading *ld) {
+    pic::TraceRange trace_("pic_init_loaded");
     if (!run || !ld) return PIC_EINVAL;
     if (run->p.precision == PIC_FP64) return PIC_EINVAL;
     LoadArgs a;
@@ -534,17 +536,20 @@ int pic_init_loaded(pic_run *run, const pic_loading *ld) {
 }
 
 int pic_set_state(pic_run *run, const void *x, const void *v, int64_t step) {
+    pic::TraceRange trace_("pic_set_state");
     if (!run || step < 0) return PIC_EINVAL;
     return load_state(run, x, v, step, Units::kPhysical);
 }
 
 int pic_set_cells(pic_run *run, const float *u, const void *v, int64_t step) {
+    pic::TraceRange trace_("pic_set_cells");
     if (!run || step < 0) return PIC_EINVAL;
     if (run->p.precision == PIC_FP64) return PIC_EINVAL;
     return load_state(run, u, v, step, Units::kCells);
 }
 
 int pic_get_cells(pic_run *run, float *u, void *v) {
+    pic::TraceRange trace_("pic_get_cells");
     if (!run) return PIC_EINVAL;
     if (run->p.precision == PIC_FP64) return PIC_EINVAL;
     if (!run->ready) return PIC_ESTATE;
@@ -556,6 +561,7 @@ int pic_get_cells(pic_run *run, float *u, void *v) {
 }
 
 int pic_deposit(pic_run *run) {
+    pic::TraceRange trace_("pic_deposit");
     if (!run) return PIC_EINVAL;
     if (!run->ready) return PIC_ESTATE;
     const size_t ng = (size_t)run->p.ncell;
@@ -567,6 +573,7 @@ int pic_deposit(pic_run *run) {
 }
 
 int pic_solve_field(pic_run *run) {
+    pic::TraceRange trace_("pic_solve_field");
     if (!run) return PIC_EINVAL;
     if (!run->ready) return PIC_ESTATE;
     PIC_CUDA(enqueue_solve(run, run->stream, run->pending_push));
@@ -576,6 +583,7 @@ int pic_solve_field(pic_run *run) {
 }
 
 int pic_push(pic_run *run) {
+    pic::TraceRange trace_("pic_push");
     if (!run) return PIC_EINVAL;
     if (!run->ready || run->pending_push) return PIC_ESTATE;
     PIC_CUDA(enqueue_push(run, run->stream, true));
@@ -584,6 +592,7 @@ int pic_push(pic_run *run) {
 }
 
 int pic_sort(pic_run *run) {
+    pic::TraceRange trace_("pic_sort");
     if (!run) return PIC_EINVAL;
     if (!run->ready) return PIC_ESTATE;
     PIC_CUDA(enqueue_sort(run, run->stream));
@@ -591,6 +600,7 @@ int pic_sort(pic_run *run) {
 }
 
 int pic_step_n(pic_run *run, int64_t n) {
+    pic::TraceRange trace_("pic_step_n");
     if (!run || n < 0) return PIC_EINVAL;
     if (!run->ready || run->pending_push) return PIC_ESTATE;
     const int64_t S = run->p.sort_interval;
@@ -632,6 +642,7 @@ int pic_sync(pic_run *run) {
 int64_t pic_step_count(const pic_run *run) { return run ? run->step : -1; }
 
 int pic_diagnostics(pic_run *run, int64_t first, int32_t count, pic_diag_row *rows) {
+    pic::TraceRange trace_("pic_diagnostics");
     if (!run || !rows || count < 0 || first < 0) return PIC_EINVAL;
     if (!run->ready) return PIC_ESTATE;
     const int64_t H = run->lay.hist_len;
@@ -653,6 +664,7 @@ int pic_diagnostics(pic_run *run, int64_t first, int32_t count, pic_diag_row *ro
 }
 
 int pic_get_state(pic_run *run, void *x, void *v) {
+    pic::TraceRange trace_("pic_get_state");
     if (!run) return PIC_EINVAL;
     if (!run->ready) return PIC_ESTATE;
     const size_t bytes = (size_t)run->p.npart * run->elem();
@@ -679,6 +691,7 @@ int pic_get_state(pic_run *run, void *x, void *v) {
 }
 
 int pic_get_field(pic_run *run, double *rho, double *phi, double *E, int64_t *rho_q) {
+    pic::TraceRange trace_("pic_get_field");
     if (!run) return PIC_EINVAL;
     if (!run->ready) return PIC_ESTATE;
     const size_t ng = (size_t)run->p.ncell;
@@ -697,6 +710,7 @@ int pic_get_field(pic_run *run, double *rho, double *phi, double *E, int64_t *rh
 
 int pic_phase_space(pic_run *run, int32_t nx, int32_t nv, double vmin, double vmax,
                     uint32_t *counts) {
+    pic::TraceRange trace_("pic_phase_space");
     if (!run || !counts || nx < 1 || nv < 1 || (long long)nx * nv > PIC_PHASE_MAX_BINS ||
         !(vmax > vmin) || !std::isfinite(vmin) || !std::isfinite(vmax))
         return PIC_EINVAL;
@@ -768,6 +782,7 @@ int pic_set_launch(pic_run *run, int32_t variant, int32_t block, int32_t unroll,
 
 int pic_autotune(pic_run *run, int32_t reps, pic_tune_entry *results,
                  int32_t max_results, int32_t *nresults) {
+    pic::TraceRange trace_("pic_autotune");
     if (!run || reps < 1) return PIC_EINVAL;
     if (!run->ready || run->pending_push) return PIC_ESTATE;
     if (nresults) *nresults = 0;
@@ -883,6 +898,7 @@ int pic_device_density(pic_run *run, void **rho_q) {
 // state is untouched (the copy's pushes deposit into the tuning density).
 int pic_tune_sort_interval(pic_run *run, const int32_t *intervals, int32_t count,
                            float *ms_per_step, int32_t *best, int32_t adopt) {
+    pic::TraceRange trace_("pic_tune_sort_interval");
     if (!run || !intervals || count < 1 || count > 64) return PIC_EINVAL;
     if (run->p.precision != PIC_FP32_FIXED) return PIC_EINVAL;
     int kmax = 8;

@@ -6,9 +6,21 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/pic.h"
 
 namespace pic {
+
+// A named NVTX range over a call of the C ABI, so that a timeline tool shows
+// each stage (push, solve, sort, step_n, pool advance, host copies) with its
+// kernels and copies; without a tool attached the calls do nothing.
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 constexpr unsigned kFull = 0xffffffffu;   // all lanes of a warp
 

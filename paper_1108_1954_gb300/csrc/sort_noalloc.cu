@@ -99,6 +99,7 @@ void geometry(long long n, int nchunk_max, int *nchunk, long long *chunk, int *n
 
 extern "C" int pic_sort_noalloc(const float *x, const float *v, float *x_out, float *v_out,
                                 int64_t n, int32_t ncell, double length, void *stream) {
+    pic::TraceRange trace_("pic_sort_noalloc");
     if (!x || !v || !x_out || !v_out) return PIC_EINVAL;
     if (n < 1 || n > (int64_t)0xFFFFFFFFll || ncell < 1 || ncell > PIC_NCELL_MAX) return PIC_EINVAL;
     if (!(length > 0.0) || !std::isfinite(length)) return PIC_EINVAL;

@@ -147,6 +147,29 @@ def test_eight_particle_groups_identical(variant, block, unroll):
         run.set_launch(variant, block, 4)           # no 4-group build of these
 
 
+def test_autotune_cache_adopts_the_stored_shape(tmp_path):
+    # a second run of the same kind takes the first run's shape from the file
+    n, ng = 200003, 1024
+    x, v = W.two_stream(n, L4PI, 0.2, 0.01, 4)
+    x32, v32 = W.to_f32_state(x, v, L4PI)
+    path = str(tmp_path / "shapes.json")
+    a = make_run(n, ng, L4PI, sort_interval=5)
+    a.init(x32, v32)
+    table = a.autotune(reps=2, cache=path)
+    assert len(table) > 1
+    shape = a.launch_shape()
+    b = make_run(n, ng, L4PI, sort_interval=5)
+    b.init(x32, v32)
+    b.set_launch(1, 256, 1)
+    assert len(b.autotune(reps=2, cache=path)) == 0         # no timing: from the file
+    assert b.launch_shape()[1:] == shape[1:]
+    a.step_n(6)
+    b.step_n(6)
+    assert np.array_equal(a.get_cells()[0], b.get_cells()[0])
+    a.close()
+    b.close()
+
+
 def test_all_particles_in_one_cell():
     # every particle in one cell: a block's low words wrap many times and the
     # carries into the high words must all be counted

@@ -57,3 +57,33 @@ def test_served_results_equal_alone():
         if r.rid not in keep:
             assert int(r.result["step"]) == r.steps
     srv.close()
+
+
+def test_resubmitted_requests_after_a_lost_worker_give_the_same_results():
+    # the worker is taken as lost after the second advance (injected on the
+    # host); the new pool reruns the resident requests from their seeds
+    reqs = small_stream(10, 2)
+    srv = serve.Server(arena_bytes=1 << 30, max_slots=6, ncell_max=1024, history=64,
+                       advance_steps=7, device="cuda:0")
+    base, _ = srv.serve(reqs)
+    again, stats = srv.serve(reqs, crash_after={2})
+    assert stats["worker_crashes"] == 1 and stats["restarts"] >= 1
+    assert any(r.restarts == 1 for r in again)
+    for a, b in zip(base, again):
+        assert a.outcome == b.outcome == "finished"
+        assert a.result.tobytes() == b.result.tobytes()      # the last row, bit for bit
+    srv.close()
+
+
+def test_a_cancelled_resident_request_frees_its_memory():
+    reqs = small_stream(4, 3)
+    reqs[0].steps = 100000                       # would run for a long time
+    reqs[0].cancel_at = 0.05
+    srv = serve.Server(arena_bytes=1 << 30, max_slots=6, ncell_max=1024, history=64,
+                       advance_steps=7, device="cuda:0")
+    recs, stats = srv.serve(reqs)
+    assert recs[0].outcome == "cancelled" and recs[0].admitted >= 0.0
+    assert all(r.outcome == "finished" for r in recs[1:])
+    assert stats["cancelled"] == 1
+    assert srv.pool.usage()[0] == 0              # every slot and byte given back
+    srv.close()

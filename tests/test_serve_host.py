@@ -5,8 +5,15 @@ diagnostics, release).  A stand-in pool with a byte budget and step counters
 checks, without a GPU: every request finishes with its own step count; a head
 request that does not fit does not block smaller ones behind it; requests that
 arrive while others are resident join the same advances (continuous
-batching); kept requests return their state, field and history.
+batching); kept requests return their state, field and history; cancelled
+requests leave the queue or give back their slot at once; a lost worker's
+resident requests are resubmitted to a new pool and finish; each request is
+logged as one JSON line.  The faults are made on the host: a stand-in pool
+that raises `WorkerLost`, or the server's own injection after an advance.
 """
+import io
+import json
+import math
 import time
 
 import numpy as np
@@ -16,12 +23,16 @@ from paper_1108_1954_gb300 import PIC_EINVAL, Loading, Params, PicError, serve
 
 
 class FakePool:
-    def __init__(self, budget, max_slots=8, history=8):
+    def __init__(self, budget, max_slots=8, history=8, lose_on_advance=None):
         self.budget, self.max_slots, self.history = budget, max_slots, history
         self.used = 0
         self.runs = {}          # slot -> [params, steps, done, bytes]
         self.next_slot = 0
         self.log = []           # (event, slot, resident count)
+        self.released = {}      # slot -> steps done when released
+        self.lose_on_advance = lose_on_advance
+        self.advances = 0
+        self.closed = False
 
     @staticmethod
     def bytes_of(p):
@@ -42,6 +53,9 @@ class FakePool:
 
     def advance(self, k):
         time.sleep(0.0005)      # an advance takes time, as on the device
+        self.advances += 1
+        if self.advances == self.lose_on_advance:
+            raise serve.WorkerLost("stand-in worker lost")
         active = 0
         for r in self.runs.values():
             if r[2] < r[1]:
@@ -68,12 +82,17 @@ class FakePool:
     def release(self, slot):
         r = self.runs.pop(slot)
         self.used -= r[3]
+        self.released[slot] = r[2]
         self.log.append(("release", slot, len(self.runs)))
 
+    def close(self):
+        self.closed = True
 
-def make_server(pool, k):
+
+def make_server(pool, k, make_pool=None):
     srv = serve.Server.__new__(serve.Server)    # no device pool
     srv.pool, srv.k, srv.history = pool, k, pool.history
+    srv.make_pool = make_pool
     return srv
 
 
@@ -155,3 +174,63 @@ def test_a_server_that_never_advances_is_refused():
     # checked before any device pool is made
     with pytest.raises(ValueError):
         serve.Server(arena_bytes=1 << 20, advance_steps=0)
+
+
+def test_cancelled_requests_leave_the_queue_or_give_back_their_slot():
+    pool = FakePool(budget=10 ** 9)
+    long = request(0, 0.0, 1000, 64, 10 ** 5)
+    long.cancel_at = 0.03                       # resident by then, far from done
+    late = request(1, 0.04, 500, 64, 30)
+    late.cancel_at = 0.0                        # cancelled as it arrives
+    plain = request(2, 0.0, 700, 64, 40)
+    log = io.StringIO()
+    recs, stats = make_server(pool, 10).serve([long, late, plain], log=log)
+    assert recs[0].outcome == "cancelled" and recs[0].cancelled >= 0.03
+    assert 0 < pool.released[0] < long.steps    # released mid-flight
+    assert recs[1].outcome == "cancelled" and recs[1].admitted == -1.0
+    assert recs[2].outcome == "finished" and int(recs[2].result["step"]) == 40
+    assert stats["cancelled"] == 2 and stats["particle_steps"] == 700 * 40
+    assert not pool.runs and pool.used == 0
+    lines = [json.loads(l) for l in log.getvalue().splitlines()]
+    assert sorted(d["rid"] for d in lines) == [0, 1, 2]
+    assert {d["rid"]: d["outcome"] for d in lines} == {0: "cancelled", 1: "cancelled",
+                                                      2: "finished"}
+
+
+@pytest.mark.parametrize("how", ["pool", "injected"])
+def test_a_lost_worker_resubmits_its_resident_requests(how):
+    pools = []
+
+    def make_pool():
+        pools.append(FakePool(budget=10 ** 9))
+        return pools[-1]
+
+    first = FakePool(budget=10 ** 9, lose_on_advance=3 if how == "pool" else None)
+    pools.append(first)
+    reqs = [request(i, 0.0, 100 * (i + 1), 64, 50) for i in range(4)]
+    reqs.append(request(4, 0.2, 300, 64, 20))    # arrives after the loss
+    log = io.StringIO()
+    srv = make_server(first, 10, make_pool)
+    recs, stats = srv.serve(reqs, log=log, crash_after={3} if how == "injected" else ())
+    assert stats["worker_crashes"] == 1 and len(pools) == 2 and first.closed
+    assert [r.restarts for r in recs] == [1, 1, 1, 1, 0]
+    for r, q in zip(recs, reqs):
+        assert r.outcome == "finished" and int(r.result["step"]) == q.steps
+    # the reruns went through the new pool from their start
+    assert [s for e, s, _ in pools[1].log if e == "admit"] == [0, 1, 2, 3, 4]
+    assert stats["restarts"] == 4 and stats["particle_steps"] == sum(
+        q.params.npart * q.steps for q in reqs)
+    lines = [json.loads(l) for l in log.getvalue().splitlines()]
+    assert {d["rid"]: d["restarts"] for d in lines} == {0: 1, 1: 1, 2: 1, 3: 1, 4: 0}
+    assert all(d["latency"] > 0 and d["particle_steps"] == d["npart"] * d["steps"]
+               for d in lines)
+
+
+def test_log_lines_of_rejected_requests():
+    pool = FakePool(budget=10 ** 5)
+    log = io.StringIO()
+    recs, stats = make_server(pool, 10).serve(
+        [request(0, 0.0, 10 ** 6, 64, 20), request(1, 0.0, 100, 64, 20)], log=log)
+    lines = {json.loads(l)["rid"]: json.loads(l) for l in log.getvalue().splitlines()}
+    assert lines[0]["outcome"] == "rejected" and "latency" not in lines[0]
+    assert lines[1]["outcome"] == "finished" and math.isfinite(lines[1]["latency"])
