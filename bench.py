@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--no-tune-batched", action="store_true")
     ap.add_argument("--pool-variant", type=int, default=1 + 16,
                     help="the pool's deposit variant (+16: 64-register build) when not tuned")
+    ap.add_argument("--pool-sort", type=int, default=0,
+                    help="the pool's sort interval when not tuned")
     ap.add_argument("--pool-cluster", type=int, default=8)
     ap.add_argument("--pool-block", type=int, default=256)
     ap.add_argument("--only-precision", action="store_true",
@@ -513,7 +515,8 @@ def time_batched(args):
     states = ensemble_states(args.batched_runs, 3)
     total_particles = sum(p.npart for p, _, _ in states)
     if args.no_tune_batched:
-        best, table, sort_table = (args.pool_variant, args.pool_cluster, args.pool_block, 0), [], []
+        best, table, sort_table = (args.pool_variant, args.pool_cluster, args.pool_block,
+                                   args.pool_sort), [], []
     else:
         best, table, sort_table = tune_pool(states, 4, H)
     S = best[3]
