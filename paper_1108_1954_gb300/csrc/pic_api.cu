@@ -422,6 +422,7 @@ int prepare_loaded(pic_run *r, int64_t step, Units units, bool aux_copy = false)
 int load_state(pic_run *r, const void *x, const void *v, int64_t step, Units units) {
     if (!x || !v) return PIC_EINVAL;
     const size_t bytes = (size_t)r->p.npart * r->elem();
+    r->ready = false;           // until the new state is loaded, checked and solved
     r->cur = 0;
     PIC_CUDA(cudaMemcpyAsync(r->xs(0), x, bytes, cudaMemcpyHostToDevice, r->stream));
     PIC_CUDA(fork_aux(r));
@@ -530,6 +531,7 @@ int pic_init_loaded(pic_run *run, const pic_loading *ld) {
     int rc = make_load_args(ld, run->p.npart, run->p.length, (float *)run->xs(0),
                             (float *)run->vs(0), &a);
     if (rc) return rc;
+    run->ready = false;
     run->cur = 0;
     PIC_CUDA(launch_load(a, run->sms, run->stream));
     return prepare_loaded(run, 0, Units::kPhysical);
