@@ -353,3 +353,32 @@ def test_ragged_sizes_identical_across_variants(n, ng):
         da, db = run.diagnostics(0, 9), ref.diagnostics(0, 9)
         assert np.allclose(da["kinetic"], db["kinetic"], rtol=1e-5)
         run.close()
+
+
+def test_partial_read_back_and_reload():
+    # pic_get_state with only x or only v (the velocities go down on the
+    # run's private stream), and pic_init from the read-back state: the same
+    # arrays and the same next steps as the full read-back
+    from paper_1108_1954_gb300 import _lib, _VP
+    n, ng = 100003, 512
+    x, v = W.two_stream(n, L4PI, 0.2, 0.01, 8)
+    x32, v32 = W.to_f32_state(x, v, L4PI)
+    run = make_run(n, ng, L4PI, sort_interval=3)
+    run.init(x32, v32)
+    run.step_n(5)
+    xa, va = run.get_state()
+    xo = np.full(n, np.nan, np.float32)
+    vo = np.full(n, np.nan, np.float32)
+    assert _lib.pic_get_state(run._h, _VP(xo.ctypes.data), None) == 0
+    assert np.array_equal(xo, xa)
+    assert _lib.pic_get_state(run._h, None, _VP(vo.ctypes.data)) == 0
+    assert np.array_equal(vo, va)
+    # the run goes on unchanged after the read-backs
+    other = make_run(n, ng, L4PI, sort_interval=3)
+    other.init(x32, v32)
+    other.step_n(9)
+    run.step_n(4)
+    assert np.array_equal(run.get_cells()[0], other.get_cells()[0])
+    assert np.array_equal(run.get_field()["rho_q"], other.get_field()["rho_q"])
+    run.close()
+    other.close()
