@@ -13,9 +13,10 @@
 //   segscan  per cell: exclusive prefix over the segments, in place, and the
 //            cell total
 //   base     exclusive prefix of the cell totals over the cells -> base[g]
-//   scatter  block b walks its chunk in order, 256 particles at a time; the
-//            warps take their slots from the per-cell cursor one after the
-//            other, so the order within a cell is the original order.
+//   scatter  block b walks its chunk in order, 512 particles at a time
+//            (64 consecutive per warp); the warps take their slots from the
+//            per-cell cursors one after the other, so the order within a
+//            cell is the original order.
 // The destination index is bounds-checked; a violation sets the device error
 // word instead of writing.
 #include "pic_internal.cuh"
@@ -178,6 +179,19 @@ __global__ void __launch_bounds__(512) sort_base_kernel(SortArgs<T> a) {
 // 2048-particle tile with coalesced writes), this plain form was the fastest
 // over the config-2 run: the others either lowered the number of resident
 // blocks whose turns interleave, or spent ~175 instructions per particle.
+// The scatter walks its chunk in rounds of kSub x 256 particles: warp w owns
+// the round's particles [32 kSub w, 32 kSub (w + 1)) as kSub steps of 32
+// (lane l takes particle 32 j + l of step j).  Lanes of one cell in a step are
+// ranked by __match_any_sync; in its turn a warp's leaders take their slots
+// from the per-cell cursors, step after step; the warps take their turns in
+// order, so a cell's particles keep their order in the chunk.  One round of
+// turns (a block barrier per warp) serves kSub x 256 particles; the next
+// round's particles are loaded a round ahead.  Measured on GB300 (2^25
+// particles after two sorts): kSub = 2, 30 registers, 134-147 us against 179
+// us for one step per turn; kSub = 3, 4 and 8 take more registers and fewer
+// blocks per SM and were slower (185, 147-152 and 199 us).
+constexpr int kSub = 2;
+
 template <typename T>
 __global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(SortArgs<T> a) {
     extern __shared__ unsigned cursor[];
@@ -191,43 +205,60 @@ __global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(SortArgs<T> 
     const long long end = min(a.n, start + a.chunk);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    // the loads run four iterations ahead (a register ring)
-    const long long bs = blockDim.x;
+    const long long round = (long long)kSub * blockDim.x;
+    // this lane's particle of step j in the round beginning at r0
+    const long long own = (long long)warp * (kSub * 32) + lane;
     auto ldx = [&](long long i) { return i < end ? __ldcs(a.x + i) : (T)0; };
     auto ldv = [&](long long i) { return i < end ? __ldcs(a.v + i) : (T)0; };
-    const long long i00 = start + threadIdx.x;
-    T x1 = ldx(i00), v1 = ldv(i00);
-    T x2 = ldx(i00 + bs), v2 = ldv(i00 + bs);
-    T x3 = ldx(i00 + 2 * bs), v3 = ldv(i00 + 2 * bs);
-    T x4 = ldx(i00 + 3 * bs), v4 = ldv(i00 + 3 * bs);
-    for (long long i0 = start; i0 < end; i0 += bs) {
-        const long long i = i0 + threadIdx.x;
-        const bool valid = i < end;
-        const T x = x1, v = v1;
-        x1 = x2; v1 = v2;
-        x2 = x3; v2 = v3;
-        x3 = x4; v3 = v4;
-        x4 = ldx(i + 4 * bs);
-        v4 = ldv(i + 4 * bs);
-        const unsigned key = valid ? cell_key(x, a.inv_dx, ng) : kNoKey;
-        const unsigned peers = __match_any_sync(kFull, key);
-        const int leader = __ffs(peers) - 1;
-        unsigned base = 0;
+    T nx[kSub], nv[kSub];
+#pragma unroll
+    for (int j = 0; j < kSub; j++) {
+        nx[j] = ldx(start + own + 32 * j);
+        nv[j] = ldv(start + own + 32 * j);
+    }
+    for (long long r0 = start; r0 < end; r0 += round) {
+        T x[kSub], v[kSub];
+#pragma unroll
+        for (int j = 0; j < kSub; j++) {
+            x[j] = nx[j];
+            v[j] = nv[j];
+            nx[j] = ldx(r0 + round + own + 32 * j);      // the next round, a round ahead
+            nv[j] = ldv(r0 + round + own + 32 * j);
+        }
+        unsigned key[kSub], peers[kSub], base[kSub];
+        int leader[kSub];
+#pragma unroll
+        for (int j = 0; j < kSub; j++) {
+            const bool valid = r0 + own + 32 * j < end;
+            key[j] = valid ? cell_key(x[j], a.inv_dx, ng) : kNoKey;
+            peers[j] = __match_any_sync(kFull, key[j]);
+            leader[j] = __ffs(peers[j]) - 1;
+            base[j] = 0u;
+        }
         for (int w = 0; w < nwarp; w++) {
-            if (w == warp && valid && lane == leader) {
-                base = cursor[key];
-                cursor[key] = base + (unsigned)__popc(peers);
+            if (w == warp) {
+#pragma unroll
+                for (int j = 0; j < kSub; j++) {
+                    if (key[j] != kNoKey && lane == leader[j]) {
+                        base[j] = cursor[key[j]];
+                        cursor[key[j]] = base[j] + (unsigned)__popc(peers[j]);
+                    }
+                    __syncwarp();
+                }
             }
             __syncthreads();
         }
-        base = __shfl_sync(kFull, base, leader);
-        if (valid) {
-            const unsigned long long dst = (unsigned long long)base + __popc(peers & lt);
-            if (dst < (unsigned long long)a.n) {
-                a.x_out[dst] = x;
-                a.v_out[dst] = v;
-            } else {
-                atomicOr(a.err, kErrSortKey);
+#pragma unroll
+        for (int j = 0; j < kSub; j++) {
+            const unsigned b = __shfl_sync(kFull, base[j], leader[j]);
+            if (key[j] != kNoKey) {
+                const unsigned long long dst = (unsigned long long)b + __popc(peers[j] & lt);
+                if (dst < (unsigned long long)a.n) {
+                    a.x_out[dst] = x[j];
+                    a.v_out[dst] = v[j];
+                } else {
+                    atomicOr(a.err, kErrSortKey);
+                }
             }
         }
     }
