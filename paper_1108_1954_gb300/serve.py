@@ -214,10 +214,24 @@ class Server:
                 advances += 1
                 if advances in crash_after:
                     raise WorkerLost("injected after advance %d" % advances)
-                done = self.pool.finished()
+                for slot in self.pool.finished():
+                    req = inflight[slot]
+                    rec = records[req.rid]
+                    if req.rid in keep:
+                        hist = (self.pool.diagnostics(slot, 0, req.steps + 1)
+                                if req.steps + 1 <= self.history else None)
+                        result = (self.pool.get_state(slot), self.pool.get_field(slot), hist)
+                    else:
+                        result = self.pool.diagnostics(slot, req.steps, 1)[0]
+                    self.pool.release(slot)
+                    # retired only once its result is read and its slot given back
+                    del inflight[slot]
+                    rec.result, rec.finished = result, now()
+                    close_record(rec)
             except WorkerLost:
                 # the resident runs are gone: a new pool, and the requests
-                # that were resident go back to the head of the queue
+                # that were resident (results not yet read included) go back
+                # to the head of the queue
                 crashes += 1
                 self._replace_pool()
                 lost = sorted(inflight.values(), key=lambda r: r.arrival)
@@ -226,18 +240,6 @@ class Server:
                     records[req.rid].restarts += 1
                     waiting.appendleft(req)
                 continue
-            for slot in done:
-                req = inflight.pop(slot)
-                rec = records[req.rid]
-                if req.rid in keep:
-                    hist = (self.pool.diagnostics(slot, 0, req.steps + 1)
-                            if req.steps + 1 <= self.history else None)
-                    rec.result = (self.pool.get_state(slot), self.pool.get_field(slot), hist)
-                else:
-                    rec.result = self.pool.diagnostics(slot, req.steps, 1)[0]
-                rec.finished = now()
-                self.pool.release(slot)
-                close_record(rec)
         wall = now()
         recs = [records[r.rid] for r in sorted(requests, key=lambda r: r.rid)]
         done = [r for r in recs if r.outcome == "finished"]

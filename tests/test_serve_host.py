@@ -23,7 +23,7 @@ from paper_1108_1954_gb300 import PIC_EINVAL, Loading, Params, PicError, serve
 
 
 class FakePool:
-    def __init__(self, budget, max_slots=8, history=8, lose_on_advance=None):
+    def __init__(self, budget, max_slots=8, history=8, lose_on_advance=None, lose_on_read=None):
         self.budget, self.max_slots, self.history = budget, max_slots, history
         self.used = 0
         self.runs = {}          # slot -> [params, steps, done, bytes]
@@ -31,6 +31,8 @@ class FakePool:
         self.log = []           # (event, slot, resident count)
         self.released = {}      # slot -> steps done when released
         self.lose_on_advance = lose_on_advance
+        self.lose_on_read = lose_on_read        # lost on this result read-back
+        self.reads = 0
         self.advances = 0
         self.closed = False
 
@@ -68,6 +70,9 @@ class FakePool:
         return [s for s, r in self.runs.items() if r[2] >= r[1]]
 
     def diagnostics(self, slot, first, count):
+        self.reads += 1
+        if self.reads == self.lose_on_read:
+            raise serve.WorkerLost("stand-in worker lost while reading a result")
         rows = np.zeros(count, dtype=[("step", "i8"), ("field", "f8")])
         rows["step"] = np.arange(first, first + count)
         return rows
@@ -234,3 +239,19 @@ def test_log_lines_of_rejected_requests():
     lines = {json.loads(l)["rid"]: json.loads(l) for l in log.getvalue().splitlines()}
     assert lines[0]["outcome"] == "rejected" and "latency" not in lines[0]
     assert lines[1]["outcome"] == "finished" and math.isfinite(lines[1]["latency"])
+
+
+def test_a_worker_lost_while_reading_results_keeps_the_unread_ones():
+    pools = []
+
+    def make_pool():
+        pools.append(FakePool(budget=10 ** 9))
+        return pools[-1]
+
+    first = FakePool(budget=10 ** 9, lose_on_read=2)     # the second result read fails
+    pools.append(first)
+    reqs = [request(i, 0.0, 100 * (i + 1), 64, 20) for i in range(3)]   # all finish together
+    recs, stats = make_server(first, 10, make_pool).serve(reqs)
+    assert stats["worker_crashes"] == 1
+    assert [r.restarts for r in recs] == [0, 1, 1]        # the first was read and retired
+    assert all(r.outcome == "finished" and int(r.result["step"]) == 20 for r in recs)
