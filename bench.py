@@ -367,18 +367,21 @@ def time_e2e(args, w, x32, v32):
     # three whole passes (upload, K steps, diagnostics and state back), timed
     # on the host clock; the mean pass
     reps = 3
-    t = time.perf_counter()
+    marks = [time.perf_counter()]
     for _ in range(reps):
         run.init(xh, vh)
         run.step_n(K)
         d = run.diagnostics(0, K)
         run.get_state(xo, vo)
-    el = (time.perf_counter() - t) / reps
+        marks.append(time.perf_counter())
+    el = (marks[-1] - marks[0]) / reps
+    _, block, variant, unroll = run.launch_shape()
     run.close()
     h2d = 2 * 4 * n
     d2h = 2 * 4 * n + d.nbytes
     return dict(value=n * K / el, seconds=el, h2d_per_step=h2d / K, d2h_per_step=d2h / K,
-                passes=reps)
+                passes=reps, pass_s=[round(b - a, 5) for a, b in zip(marks, marks[1:])],
+                launch={"block": block, "deposit_variant": variant, "unroll": unroll})
 
 
 def time_sharded(args, w, x32, v32):
@@ -1053,7 +1056,8 @@ def main():
                        "h2d_bytes_per_step": e2e["h2d_per_step"],
                        "d2h_bytes_per_step": e2e["d2h_per_step"],
                        "timing": "host clock, mean of %d whole passes (upload, steps, "
-                                 "diagnostics and state back)" % e2e["passes"]}
+                                 "diagnostics and state back)" % e2e["passes"],
+                       "pass_s": e2e["pass_s"], "launch": e2e["launch"]}
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if sharded is not None:
