@@ -24,7 +24,7 @@ def run_set():
     """Runs of different sizes, grids and beams (ragged N, tiny N and NG)."""
     specs = [(20000, 64, 0.2, 0.01), (100003, 2048, 0.35, 0.02), (4099, 200, 0.1, 0.0),
              (5, 16, 0.3, 0.05), (1, 1, 0.2, 0.0), (77777, 512, 0.05, 0.001),
-             (250001, 1024, 0.5, 0.03), (3, 7, 0.2, 0.01)]
+             (250001, 1024, 0.5, 0.03), (3, 7, 0.2, 0.01), (65537, 4096, 0.2, 0.01)]
     out = []
     for i, (n, ng, v0, vth) in enumerate(specs):
         x, v = W.two_stream(n, L4PI, v0, vth, 100 + i)
