@@ -445,8 +445,9 @@ def tune_pool(states, steps, history):
     The whole ensemble is admitted once; each (variant, cluster, block) is
     timed over `steps` steps (after one untimed step) in each of three
     rounds, on the same resident runs, the shape changed with
-    pic_pool_configure and the order shuffled per round.  Then, with the
-    fastest shape, the ensemble is admitted again for each sort interval S
+    pic_pool_configure and the order shuffled per round; the leading three
+    are timed again over longer windows later in a fresh ensemble.  Then,
+    with the fastest shape, the ensemble is admitted again for each sort interval S
     and timed over 40 steps (after 10), long enough to include the sorts of
     every S tried.  Returns the fastest (variant, cluster, block, S) and the
     two tables."""
@@ -498,7 +499,26 @@ def tune_pool(states, steps, history):
             total[sh] += e0.elapsed_time(e1)
     pool.close()
     table = sorted(((sh, t / rounds) for sh, t in total.items()), key=lambda t: t[1])
-    shape = table[0][0]
+    # The short windows rank the shapes within a few percent; the leading
+    # three are timed again in longer windows spread over steps 100-400 of
+    # a fresh ensemble, where most of the run's time goes.
+    top = [sh for sh, _ in table[:3]]
+    pool = admit_all(0)
+    pool.configure(*top[0])
+    pool.advance(100)
+    long_total = {sh: 0.0 for sh in top}
+    for _ in range(4):
+        for i in rng.permutation(len(top)):
+            sh = top[i]
+            pool.configure(*sh)
+            pool.advance(1)
+            e0.record(pool.stream)
+            pool.advance(24)
+            e1.record(pool.stream)
+            pool.sync()
+            long_total[sh] += e0.elapsed_time(e1)
+    pool.close()
+    shape = min(top, key=lambda sh: long_total[sh])
     sort_table = []
     for S in (0, 10, 20, 40):
         pool = admit_all(S)

@@ -45,7 +45,7 @@ namespace cg = cooperative_groups;
 namespace pic {
 namespace {
 
-constexpr int kU = 2;                   // float4 groups per thread per iteration
+constexpr int kU = 1;                   // float4 groups per thread per iteration (one: fewer spills in the 64-register build)
 constexpr int kMaxCluster = 8;          // blocks per cluster (portable limit)
 
 // The part of a block's shared memory its peers read.
