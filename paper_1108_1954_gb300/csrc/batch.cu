@@ -13,12 +13,14 @@
 //      fixed-point tile -- the same device code as the single-run push;
 //      cluster barrier;
 //   B  each block sums the C tiles over its node slice through distributed
-//      shared memory, forms R_g = N 2^24 - NG rho_q[g] and the slice sums
-//      sum R, sum g R; cluster barrier; from all slices' sums it has the
-//      prefixes the exact integer solve needs (as in field.cu) and computes
-//      E (Eq. 7 via the flux form of Eq. 6) for its slice in 128-bit integers,
-//      float64 at the last conversion; cluster barrier;
-//   C  each block copies the other slices of E into its own shared copy;
+//      shared memory, forms R_g = N 2^24 - NG rho_q[g], scans R and g R over
+//      its slice and takes the slice sums from the scan's warp totals;
+//      cluster barrier; from all slices' sums it has the prefixes the exact
+//      integer solve needs (as in field.cu) and computes E (Eq. 7 via the
+//      flux form of Eq. 6) for its slice in 128-bit integers, float64 at the
+//      last conversion; cluster barrier;
+//   C  each block copies the other slices of E into its own shared copy
+//      (one node of each peer per thread, no division by the slice size);
 //      block 0 sums the slice diagnostics over the blocks and writes the
 //      step's history rows just before the next step's first barrier.
 // A run with a sort interval S > 0 first sorts its particles by cell before
@@ -189,7 +191,7 @@ __device__ void cluster_sort(const BatchArgs &a, cg::cluster_group &cl, Exchange
 
 template <int VARIANT>
 __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_group &cl,
-                          Exchange &ex, Tile &tile, float *sE, i128 *sh128, double *shd,
+                          Exchange &ex, Tile &tile, float *sE, double *shd,
                           float *shf) {
     __shared__ i128 pre[4];
     __shared__ __align__(16) unsigned long long scan64[4 * 32];
@@ -354,10 +356,18 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
             }
         }
         const i128 Rg = mine ? (i128)ntot - (i128)ng * (i128)rq : (i128)0;
-        {
-            i128 S0 = Rg, S1 = Rg * (i128)g, Sz = 0;
-            block_sum3_i128(S0, S1, Sz, sh128);
-            if (tid == 0) { ex.s0 = S0; ex.s1 = S1; }
+        // one pass of the slice's inclusive scans of R_k and k R_k (the
+        // slice alone: no peer's words), and the slice sums from their warp
+        // totals
+        const I128Pair sc = block_inclusive_scan2_i128(Rg, Rg * (i128)g, scan64);
+        if (tid == 0) {
+            i128 S0 = 0, S1 = 0;
+            for (int w = 0; w < (bs >> 5); w++) {
+                S0 += (i128)(((unsigned __int128)scan64[32 + w] << 64) | scan64[w]);
+                S1 += (i128)(((unsigned __int128)scan64[96 + w] << 64) | scan64[64 + w]);
+            }
+            ex.s0 = S0;
+            ex.s1 = S1;
         }
         cl.sync();                                                    // #2
 
@@ -371,7 +381,8 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
                 v1 = pe->s1;
             }
             i128 a0 = tid < r ? v0 : (i128)0, bb = tid < r ? v1 : (i128)0;
-            for (int o = 16; o > 0; o >>= 1) {
+            // lanes C.. hold zeros: kMaxCluster lanes carry the sums
+            for (int o = kMaxCluster / 2; o > 0; o >>= 1) {
                 a0 += shfl_down_i128(a0, o);
                 bb += shfl_down_i128(bb, o);
                 v0 += shfl_down_i128(v0, o);
@@ -382,8 +393,6 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
         __syncthreads();
         const i128 A0 = pre[0], B = pre[1], SR = pre[2], SS1 = pre[3];
         const i128 SP = (i128)ng * SR - SS1;          // sum_k (NG-k) R_k
-        // one pass of the slice's inclusive scans of R_k and k R_k
-        const I128Pair sc = block_inclusive_scan2_i128(Rg, Rg * (i128)g, scan64);
         const i128 Pg = A0 + sc.a;                                          // P_g
         const i128 M = (i128)ng * Pg - SP;                                  // M_g
         // M_{g-1} = NG P_{g-1} - SP with P_{g-1} = P_g - R_g; M_{-1} = M_{NG-1}
@@ -466,24 +475,28 @@ __device__ void run_steps(const BatchArgs &a, const BatchRun &R, cg::cluster_gro
         }
         cl.sync();                                                    // #3
 
-        // ---- C: the other slices of E into the own copy (kCopy remote
-        // loads in flight per thread)
-        constexpr int kCopy = 8;
-        for (int j0 = tid; j0 < ng + 2; j0 += kCopy * bs) {
-            float e[kCopy];
+        // ---- C: the other slices of E into the own copy: thread t takes
+        // node o P + t of every peer o (a slice has at most one node per
+        // thread), all remote loads in flight together; then the tile is
+        // cleared for the next step
+        {
+            float e[kMaxCluster];
 #pragma unroll
-            for (int k = 0; k < kCopy; k++) {
-                const int j = j0 + k * bs;
-                const int g = j == 0 ? ng - 1 : (j == ng + 1 ? 0 : j - 1);
-                const int owner = g / P;
-                e[k] = (j < ng + 2 && owner != r) ? cl.map_shared_rank(sE, owner)[j] : 0.0f;
+            for (int o = 0; o < kMaxCluster; o++) {
+                const int go = o * P + tid;
+                e[o] = (o < C && o != r && tid < P && go < ng) ? cl.map_shared_rank(sE, o)[go + 1]
+                                                                : 0.0f;
             }
 #pragma unroll
-            for (int k = 0; k < kCopy; k++) {
-                const int j = j0 + k * bs;
-                if (j >= ng + 2) break;
-                const int g = j == 0 ? ng - 1 : (j == ng + 1 ? 0 : j - 1);
-                if (g / P != r) sE[j] = e[k];
+            for (int o = 0; o < kMaxCluster; o++) {
+                const int go = o * P + tid;
+                if (o < C && o != r && tid < P && go < ng) {
+                    sE[go + 1] = e[o];
+                    if (go == ng - 1) sE[0] = e[o];
+                    if (go == 0) sE[ng + 1] = e[o];
+                }
+            }
+            for (int j = tid; j < ng + 2; j += bs) {
                 tile.lo[j] = 0u;
                 tile.hi[j] = 0u;
             }
@@ -500,7 +513,6 @@ template <int VARIANT, int MINB>
 __global__ void __launch_bounds__(512, MINB) pic_batch_kernel(BatchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Exchange ex;
-    __shared__ i128 sh128[96];
     __shared__ __align__(16) double shd[32 * 3];
     __shared__ __align__(16) float shf[32 * 2 * PIC_NMODES];
     cg::cluster_group cl = cg::this_cluster();
@@ -519,7 +531,7 @@ __global__ void __launch_bounds__(512, MINB) pic_batch_kernel(BatchArgs a) {
         if (ticket >= a.nrun) break;
         const BatchRun R = a.runs[a.order[ticket]];
         if (!(a.push && R.steps == 0))
-            run_steps<VARIANT>(a, R, cl, ex, tile, sE, sh128, shd, shf);
+            run_steps<VARIANT>(a, R, cl, ex, tile, sE, shd, shf);
         cl.sync();
     }
 }
