@@ -445,8 +445,8 @@ def tune_pool(states, steps, history):
     The whole ensemble is admitted once; each (variant, cluster, block) is
     timed over `steps` steps (after one untimed step) in each of three
     rounds, on the same resident runs, the shape changed with
-    pic_pool_configure and the order shuffled per round; the leading three
-    are timed again over longer windows later in a fresh ensemble.  Then,
+    pic_pool_configure and the order shuffled per round; the leading six
+    are timed again over steps 100-500 of a fresh ensemble.  Then,
     with the fastest shape, the ensemble is admitted again for each sort interval S
     and timed over 40 steps (after 10), long enough to include the sorts of
     every S tried.  Returns the fastest (variant, cluster, block, S) and the
@@ -500,9 +500,9 @@ def tune_pool(states, steps, history):
     pool.close()
     table = sorted(((sh, t / rounds) for sh, t in total.items()), key=lambda t: t[1])
     # The short windows rank the shapes within a few percent; the leading
-    # three are timed again in longer windows spread over steps 100-400 of
-    # a fresh ensemble, where most of the run's time goes.
-    top = [sh for sh, _ in table[:3]]
+    # six are timed again in windows spread over steps 100-500 of a fresh
+    # ensemble, where most of the run's time goes.
+    top = [sh for sh, _ in table[:6]]
     pool = admit_all(0)
     pool.configure(*top[0])
     pool.advance(100)
@@ -513,7 +513,7 @@ def tune_pool(states, steps, history):
             pool.configure(*sh)
             pool.advance(1)
             e0.record(pool.stream)
-            pool.advance(24)
+            pool.advance(16)
             e1.record(pool.stream)
             pool.sync()
             long_total[sh] += e0.elapsed_time(e1)
