@@ -293,14 +293,15 @@ __device__ void cluster_finish(const SolveArgs &a, cg::cluster_group &cl, Cluste
 //
 // The same exact integer solve with the nodes split into C <= 16 slices of
 // ceil(NG/C) nodes: one slice per block of a cluster, one node per thread.
-// Each block reads (and clears) only its own slice of the accumulator and
-// publishes its slice sums sum_k R_k and sum_k k R_k in shared memory.  After
-// a cluster barrier every block forms, from all slices' sums (one remote read
+// Each block reads (and clears) only its own slice of the accumulator, takes
+// one block pass of two inclusive scans over its slice, of R_k and of k R_k
+// (I and J below, over b0 <= k <= g), and publishes its slice sums sum_k R_k
+// and sum_k k R_k (the scans' warp totals, summed) in shared memory.  After a
+// cluster barrier every block forms, from all slices' sums (one remote read
 // per lane of warp 0; integer sums, so the order does not matter),
 //   A0 = sum_{k<b0} R_k,  B = sum_{k<b0} k R_k,
 //   SR = sum_k R_k,       SP = NG SR - sum_k k R_k,
-// and solves its slice with one block pass of two inclusive scans, of R_k and
-// of k R_k (I and J below, over b0 <= k <= g): P_g = A0 + I, M_g = NG P_g - SP,
+// and solves its slice: P_g = A0 + I, M_g = NG P_g - SP,
 // M_{g-1} = NG (P_g - R_g) - SP (M_{-1} = NG SR - SP), and
 // sum_{k<g} P_k = g P_g - (B + J); then the diagnostics (cluster_finish).
 // Three cluster barriers, no global atomics.
@@ -312,7 +313,6 @@ __global__ void __launch_bounds__(kClusterSolveThreads) pic_solve_cluster_kernel
     cg::cluster_group cl = cg::this_cluster();
     __shared__ SliceSums ex;
     __shared__ ClusterDiag cd;
-    __shared__ i128 sh[96];
     __shared__ i128 pre[4];
     __shared__ __align__(16) unsigned long long scan64[4 * 32];
     const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
@@ -333,10 +333,16 @@ __global__ void __launch_bounds__(kClusterSolveThreads) pic_solve_cluster_kernel
     double kv[2];
     push_sums_share(a, C, r, kv);
     const i128 R = mine ? (i128)ntot - (i128)ng * (i128)q : (i128)0;
-    {
-        i128 S0 = R, S1 = R * (i128)g, Sz = 0;
-        block_sum3_i128(S0, S1, Sz, sh);
-        if (t == 0) { ex.s0 = S0; ex.s1 = S1; }
+    // one pass of the slice's inclusive scans of R_k and k R_k
+    const I128Pair sc = block_inclusive_scan2_i128(R, R * (i128)g, scan64);
+    if (t == 0) {
+        i128 S0 = 0, S1 = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+            S0 += (i128)(((unsigned __int128)scan64[32 + w] << 64) | scan64[w]);
+            S1 += (i128)(((unsigned __int128)scan64[96 + w] << 64) | scan64[64 + w]);
+        }
+        ex.s0 = S0;
+        ex.s1 = S1;
     }
     cl.sync();                                                        // #1
 
@@ -348,7 +354,8 @@ __global__ void __launch_bounds__(kClusterSolveThreads) pic_solve_cluster_kernel
             v1 = pe->s1;
         }
         i128 a0 = t < r ? v0 : (i128)0, bb = t < r ? v1 : (i128)0;
-        for (int o = 16; o > 0; o >>= 1) {
+        // lanes C.. hold zeros: kMaxSolveCluster lanes carry the sums
+        for (int o = kMaxSolveCluster / 2; o > 0; o >>= 1) {
             a0 += shfl_down_i128(a0, o);
             bb += shfl_down_i128(bb, o);
             v0 += shfl_down_i128(v0, o);
@@ -359,8 +366,6 @@ __global__ void __launch_bounds__(kClusterSolveThreads) pic_solve_cluster_kernel
     __syncthreads();
     const i128 A0 = pre[0], B = pre[1], SR = pre[2], SS1 = pre[3];
     const i128 SP = (i128)ng * SR - SS1;          // sum_k (NG-k) R_k
-    // one pass of the slice's inclusive scans of R_k and k R_k
-    const I128Pair sc = block_inclusive_scan2_i128(R, R * (i128)g, scan64);
     const i128 P = A0 + sc.a;                                          // P_g
     const i128 M = (i128)ng * P - SP;                                  // M_g
     // M_{g-1} = NG P_{g-1} - SP with P_{g-1} = P_g - R_g; M_{-1} = M_{NG-1}
